@@ -1,0 +1,166 @@
+/*
+ * geotrace.h -- C ABI of the GB300 (sm_103a) null-geodesic ray tracer.
+ *
+ * The library integrates one light ray per image pixel backwards from a pinhole
+ * camera through a rotating black-hole spacetime with parameters (M, S, Q):
+ * Kerr in Boyer-Lindquist coordinates (Sec. 2.2.2 of "Graphical Processing of
+ * Geodesic Propagation in Python") when Q = 0, Manko-Novikov with quadrupole
+ * deviation q = Q (Sec. 2.2.3) otherwise.  Each ray follows the Hamiltonian
+ * equations of Eq. hamGeodesic,
+ *     dq^mu/dtau = g^{mu nu} p_nu,     dp_mu/dtau = -1/2 d_mu g^{nu sigma} p_nu p_sigma,
+ * under classical RK4 (Sec. 3.1.2) with the step h = step_precision/|dq^t/dtau|
+ * taken from the first stage, and stops (appendix listing, propagation kernel)
+ *     ESCAPED   when r > 1.5 r0 after a step,
+ *     HORIZON   when the step just taken had h < step_precision * 3e-5,
+ *     MAXSTEPS  after n_steps steps,
+ *     NONFINITE when a step produces a non-finite value (the last finite state is kept).
+ * Initial data (Sec. 3.3.1 and the listing's camera block): pixel (i, j), i along phi
+ * in [0, res_x), j along theta in [0, res_y), direction v = (v^t, -1, beta_j,
+ * alpha_i/sin theta0) with alpha_i, beta_j the inclusive linspaces over [-H, H],
+ * [-V, V], V = tan(FOV/2)/r0, H = atan(tan(V) res_x/res_y); v^t from the null
+ * condition, v rescaled so that v^t = -1, p_mu = g_{mu nu} v^nu at (0, r0, theta0, 0).
+ *
+ * Conventions
+ *   - Every function returns GT_OK (0) or a negative GT_ERR_* code; nothing throws.
+ *   - Output arrays of gt_trace / gt_trace_batch are DEVICE memory owned by the
+ *     caller, one element per ray, flat index j*res_x + i (rows along theta).
+ *     t, r, theta, phi are float64 (also in the FP32-mixed mode); status is uint8
+ *     (GT_RAY_*), nsteps is uint32 and counts the terminal step.
+ *   - Calls are asynchronous on the context's stream (a borrowed cudaStream_t,
+ *     0 = legacy default stream); gt_sync waits for it.  Output pointers must stay
+ *     valid until the work completes.
+ *   - A context is bound to one device, is not thread-safe, and owns only small
+ *     scratch memory (queue counters, camera descriptors), freed by gt_destroy.
+ */
+#ifndef GEOTRACE_H
+#define GEOTRACE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define GT_OK 0
+#define GT_ERR_INVALID_ARG (-1)    /* bad parameter, null or misaligned pointer */
+#define GT_ERR_NOT_CONFIGURED (-2) /* spacetime or camera not set */
+#define GT_ERR_CUDA (-3)           /* a CUDA runtime call failed */
+#define GT_ERR_OOM (-4)            /* device allocation failed */
+#define GT_ERR_TIMEOUT (-5)        /* the device watchdog stopped the launch */
+#define GT_ERR_UNSUPPORTED (-6)    /* no sm_103 device / feature not built */
+
+/* per-ray status */
+#define GT_RAY_ESCAPED 0
+#define GT_RAY_HORIZON 1
+#define GT_RAY_MAXSTEPS 2
+#define GT_RAY_NONFINITE 3
+#define GT_RAY_TIMEOUT 4
+
+/* arithmetic modes */
+#define GT_MODE_FP64 0       /* FP64 end to end */
+#define GT_MODE_FP32_MIXED 1 /* FP32 RK4 with compensated state; FP64 zone and H = 0 re-projection */
+
+/* option flags */
+#define GT_FLAG_COMPAT_WEIGHTS 1 /* RK4 weights 0.1667 as printed in the listing (default 1/6) */
+#define GT_FLAG_COMPAT_CAMERA 2  /* v^phi = alpha_i as in the listing (default alpha_i/sin theta0) */
+#define GT_FLAG_ONE_SHOT 4       /* one ray per thread instead of the persistent ray queue */
+
+typedef struct gt_ctx gt_ctx;
+
+/* Launch and precision options; zero fields take the defaults noted. */
+typedef struct gt_options {
+    int block_size;          /* threads per block, multiple of 32 in [32, 256]; 0 = 128 */
+    int blocks_per_sm;       /* persistent grid = min(blocks_per_sm, resident limit) * SMs; 0 = 4 */
+    int flags;               /* GT_FLAG_* */
+    int reproject_every;     /* FP32-mixed: steps between H = 0 re-projections; 0 = 64 */
+    double r_switch;         /* FP32-mixed: FP64 zone r < r_switch; 0 = automatic, < 0 = none */
+    double timeout_seconds;  /* device watchdog (wall clock per launch); 0 = none */
+} gt_options;
+
+/* One camera of a batch (gt_trace_batch); same meaning as gt_set_spacetime and
+ * gt_set_camera.  Rays of camera c occupy flat ids [offset_c, offset_c + res_x*res_y)
+ * with offset_c the sum of the preceding cameras' pixel counts. */
+typedef struct gt_camera_desc {
+    double M, S, Q;
+    double r0, theta0, fov_deg;
+    int32_t res_x, res_y;
+} gt_camera_desc;
+
+/* Create a context on CUDA device `device` issuing work on `cuda_stream`
+ * (a cudaStream_t owned by the caller, e.g. torch's current stream; NULL = the
+ * legacy default stream).  Allocates the context's scratch memory.
+ * Errors: GT_ERR_INVALID_ARG (out == NULL), GT_ERR_UNSUPPORTED (device is not
+ * compute capability 10.3), GT_ERR_CUDA, GT_ERR_OOM. */
+int gt_create(gt_ctx **out, int device, void *cuda_stream);
+
+/* Synchronise the context's stream and free everything the context owns. */
+int gt_destroy(gt_ctx *ctx);
+
+/* Replace the stream later calls are issued on (the old stream is not synchronised). */
+int gt_set_stream(gt_ctx *ctx, void *cuda_stream);
+
+/* Spacetime (Sec. 2.2): mass M > 0, spin S with |S| < M^2 (Sec. 2.2.2), Q the
+ * Manko-Novikov quadrupole deviation q (Sec. 2.2.3); Q != 0 requires S != 0
+ * because alpha divides by S/M.  Errors: GT_ERR_INVALID_ARG. */
+int gt_set_spacetime(gt_ctx *ctx, double M, double S, double Q);
+
+/* Pinhole camera (Sec. 3.3.1): position (0, r0, theta0, 0) with r0 > 0,
+ * 0 < theta0 < pi (radians), full vertical field of view 0 < fov_deg < 180
+ * (degrees), res_x, res_y >= 1.  The camera must sit where g_tt < 0 (outside
+ * the ergoregion); gt_trace reports GT_ERR_INVALID_ARG otherwise. */
+int gt_set_camera(gt_ctx *ctx, double r0, double theta0, double fov_deg, int res_x, int res_y);
+
+/* Options for later calls; opts == NULL restores the defaults. */
+int gt_set_options(gt_ctx *ctx, const gt_options *opts);
+
+/* Trace every pixel of the configured camera (n_steps >= 0 RK4 steps at most,
+ * step_precision > 0, mode GT_MODE_*).  Outputs: device arrays of res_x*res_y
+ * elements, 8-byte aligned for the float64 ones; any of t, r, theta, phi, status,
+ * nsteps may be NULL to skip it.  Asynchronous; on a watchdog stop the call
+ * returns GT_ERR_TIMEOUT after synchronising, and unfinished rays carry
+ * GT_RAY_TIMEOUT.  Errors: GT_ERR_NOT_CONFIGURED, GT_ERR_INVALID_ARG, GT_ERR_CUDA,
+ * GT_ERR_TIMEOUT. */
+int gt_trace(gt_ctx *ctx, int64_t n_steps, double step_precision, int mode, double *t, double *r,
+             double *theta, double *phi, uint8_t *status, uint32_t *nsteps);
+
+/* As gt_trace, restricted to the contiguous flat pixel range [first, first + count)
+ * of the configured camera; output element k belongs to pixel first + k.  Used to
+ * shard one image across devices or processes and to sample long runs.
+ * Errors as gt_trace, plus GT_ERR_INVALID_ARG when the range leaves the image. */
+int gt_trace_range(gt_ctx *ctx, int64_t first, int64_t count, int64_t n_steps,
+                   double step_precision, int mode, double *t, double *r, double *theta,
+                   double *phi, uint8_t *status, uint32_t *nsteps);
+
+/* As gt_trace, but the outputs are HOST arrays: the library copies the results
+ * back (through its own device staging buffers) and returns after they arrived. */
+int gt_trace_host(gt_ctx *ctx, int64_t n_steps, double step_precision, int mode, double *t,
+                  double *r, double *theta, double *phi, uint8_t *status, uint32_t *nsteps);
+
+/* Trace n_cams cameras (host array of descriptors) in one persistent launch.  Outputs
+ * are device arrays over the flattened id space (sum of res_x*res_y).  Errors as gt_trace. */
+int gt_trace_batch(gt_ctx *ctx, const gt_camera_desc *cams, int n_cams, int64_t n_steps,
+                   double step_precision, int mode, double *t, double *r, double *theta,
+                   double *phi, uint8_t *status, uint32_t *nsteps);
+
+/* Wait for all work issued by the context. */
+int gt_sync(gt_ctx *ctx);
+
+/* Number of streaming multiprocessors of the context's device (for grid sizing). */
+int gt_device_sm_count(gt_ctx *ctx, int *out);
+
+/* Measure the device's FMA throughput (FP64 when fp64 != 0, else FP32) with a
+ * synthetic kernel of independent FMA chains: grid 8 x SMs x 256 threads, `iters`
+ * x 128 FMAs per thread, timed with CUDA events on the legacy stream.  Writes
+ * FLOP/s (2 per FMA).  Used as the ALU roofline denominator; not part of the
+ * paper's method.  Errors: GT_ERR_INVALID_ARG, GT_ERR_CUDA. */
+int gt_measure_fma_peak(int device, int fp64, int iters, double *flops_per_s);
+
+/* Static description of an error code; never NULL. */
+const char *gt_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GEOTRACE_H */

@@ -1,0 +1,277 @@
+// spacetime.cuh -- device-side spacetimes for the geodesic integrator (sm_103a).
+//
+// For a stationary, axisymmetric metric g^{mu nu}(r, theta) the Hamiltonian of
+// Eq. hamGeodesic is H = 1/2 g^{mu nu} p_mu p_nu, with p_t and p_phi constants of
+// motion.  Rather than the paper's 4x4x4 contraction of finite-difference
+// derivatives (appendix listing), each spacetime here writes H in closed form and
+// differentiates it exactly:
+//
+//   Kerr (Sec. 2.2.2), with Sigma = r^2 + a^2 cos^2, Delta = r^2 - 2Mr + a^2:
+//     2 Sigma H = K = Delta p_r^2 + p_theta^2 + V^2 - W^2/Delta,
+//     W = (r^2 + a^2) p_t + a p_phi,   V = p_phi/sin + a sin p_t,
+//   and dq/dtau = dH/dp, dp_r/dtau = -dH/dr, dp_theta/dtau = -dH/dtheta by hand.
+//
+//   Manko-Novikov (Sec. 2.2.3): the inverse metric of its line element is
+//     2H = -p_t^2/f + F (p_phi + w p_t)^2 + G (Delta p_r^2 + p_theta^2),
+//     F = f/(Delta sin^2),  G = g^{theta theta} = (1-alpha^2)^2/k^2 exp(2psi - 2gamma'')/B,
+//   (gamma'' = gamma' without its logarithm, which cancels against e^{2gamma}'s
+//   (x^2-1) factor), and the r and theta derivatives come from forward-mode dual
+//   numbers (value, d/dr, d/dtheta) carried through every operation.
+//
+// Both are written once over a scalar type T so the FP32-mixed path can reuse them.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#ifndef GT_HD
+#define GT_HD __host__ __device__ __forceinline__
+#endif
+
+namespace gt {
+
+enum : int { KIND_KERR = 0, KIND_MN = 1 };
+
+// Derived constants of one spacetime (computed on the device by the setup kernel).
+struct SpacetimeC {
+    int kind;
+    double M, a, a2;           // Kerr: a = S/M
+    double r_plus;             // outer horizon (Kerr M + sqrt(M^2 - a^2); MN M + k)
+    double k, ik, alpha, beta; // Manko-Novikov
+    double two_beta, three_beta2;
+    double c_g;                // (1 - alpha^2)^2 / k^2
+    double w_inf;              // 4 k alpha / (1 - alpha^2)
+    double k2, two_k;
+};
+
+template <class T>
+struct Rates {
+    T dt, dr, dth, dph, dpr, dpth;
+};
+
+// ------------------------------------------------------------------ math helpers
+// (device-only; a host-side counting type supplies its own overloads)
+#ifdef __CUDACC__
+__device__ __forceinline__ void sincos_t(double x, double *s, double *c) { sincos(x, s, c); }
+__device__ __forceinline__ void sincos_t(float x, float *s, float *c) { sincosf(x, s, c); }
+__device__ __forceinline__ double exp_t(double x) { return exp(x); }
+__device__ __forceinline__ float exp_t(float x) { return expf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+#endif
+
+// ------------------------------------------------------------------ dual numbers
+// (value, d/dr, d/dtheta)
+template <class T>
+struct D3 {
+    T v, r, t;
+};
+
+template <class T>
+GT_HD D3<T> dc(T v) { return {v, T(0), T(0)}; }
+template <class T>
+GT_HD D3<T> operator+(D3<T> a, D3<T> b) { return {a.v + b.v, a.r + b.r, a.t + b.t}; }
+template <class T>
+GT_HD D3<T> operator-(D3<T> a, D3<T> b) { return {a.v - b.v, a.r - b.r, a.t - b.t}; }
+template <class T>
+GT_HD D3<T> operator-(D3<T> a) { return {-a.v, -a.r, -a.t}; }
+template <class T>
+GT_HD D3<T> operator+(D3<T> a, T c) { return {a.v + c, a.r, a.t}; }
+template <class T>
+GT_HD D3<T> operator+(T c, D3<T> a) { return {a.v + c, a.r, a.t}; }
+template <class T>
+GT_HD D3<T> operator-(D3<T> a, T c) { return {a.v - c, a.r, a.t}; }
+template <class T>
+GT_HD D3<T> operator-(T c, D3<T> a) { return {c - a.v, -a.r, -a.t}; }
+template <class T>
+GT_HD D3<T> operator*(D3<T> a, T c) { return {a.v * c, a.r * c, a.t * c}; }
+template <class T>
+GT_HD D3<T> operator*(T c, D3<T> a) { return {a.v * c, a.r * c, a.t * c}; }
+template <class T>
+GT_HD D3<T> operator*(D3<T> a, D3<T> b)
+{
+    return {a.v * b.v, fma_t(a.r, b.v, a.v * b.r), fma_t(a.t, b.v, a.v * b.t)};
+}
+template <class T>
+GT_HD D3<T> dsq(D3<T> a)
+{
+    const T tv = a.v + a.v;
+    return {a.v * a.v, tv * a.r, tv * a.t};
+}
+template <class T>
+GT_HD D3<T> drcp(D3<T> a)
+{
+    const T iv = T(1) / a.v;
+    const T w = -iv * iv;
+    return {iv, a.r * w, a.t * w};
+}
+template <class T>
+GT_HD D3<T> drsqrt(D3<T> a)
+{
+    const T rs = rsqrt_t(a.v);
+    const T w = T(-0.5) * rs * rs * rs;
+    return {rs, a.r * w, a.t * w};
+}
+template <class T>
+GT_HD D3<T> dexp(D3<T> a)
+{
+    const T e = exp_t(a.v);
+    return {e, a.r * e, a.t * e};
+}
+
+// ------------------------------------------------------------------ Kerr
+template <class T>
+GT_HD void kerr_rates(const SpacetimeC &c, T r, T th, T pr, T pth, T pt,
+                                           T pph, Rates<T> &o)
+{
+    T s, cs;
+    sincos_t(th, &s, &cs);
+    const T a = T(c.a), a2 = T(c.a2), M = T(c.M);
+    const T r2 = r * r, ra2 = r2 + a2;
+    const T s2 = s * s;
+    const T Sigma = fma_t(a2, cs * cs, r2);
+    const T Delta = fma_t(r, r - T(2) * M, a2);
+    const T inv = T(1) / (Sigma * Delta * s2); // one division for 1/Sigma, 1/Delta, 1/sin^2
+    const T iSigma = Delta * s2 * inv;
+    const T iDelta = Sigma * s2 * inv;
+    const T is2 = Sigma * Delta * inv;
+    const T is = s * is2;
+    const T W = fma_t(ra2, pt, a * pph);
+    const T V = fma_t(pph, is, a * s * pt);
+    const T WiD = W * iDelta;
+    const T K = fma_t(Delta * pr, pr, fma_t(pth, pth, fma_t(V, V, -W * WiD)));
+    o.dr = Delta * pr * iSigma;
+    o.dth = pth * iSigma;
+    o.dt = (a * V * s - ra2 * WiD) * iSigma;
+    o.dph = (V * is - a * WiD) * iSigma;
+    const T Kr = T(2) * (r - M) * fma_t(pr, pr, WiD * WiD) - T(4) * r * pt * WiD;
+    const T Kth = T(2) * V * cs * (a * pt - pph * is2);
+    const T KiS = K * iSigma;
+    o.dpr = T(-0.5) * (Kr - T(2) * r * KiS) * iSigma;
+    o.dpth = T(-0.5) * fma_t(T(2) * a2 * s * cs, KiS, Kth) * iSigma;
+}
+
+#ifdef __CUDACC__
+// Inverse-metric components (tt, t phi, phi phi, rr, theta theta) of Kerr.
+__device__ __forceinline__ void kerr_upper(const SpacetimeC &c, double r, double th, double g[5])
+{
+    double s, cs;
+    sincos(th, &s, &cs);
+    const double a = c.a, a2 = c.a2, M = c.M;
+    const double s2 = s * s, ra2 = r * r + a2;
+    const double Sigma = r * r + a2 * cs * cs;
+    const double Delta = r * r - 2.0 * M * r + a2;
+    const double D = Sigma * Delta;
+    g[0] = -(ra2 * ra2 - a2 * Delta * s2) / D;
+    g[1] = -2.0 * M * a * r / D;
+    g[2] = (Delta - a2 * s2) / (D * s2);
+    g[3] = Delta / Sigma;
+    g[4] = 1.0 / Sigma;
+}
+#endif
+
+// ------------------------------------------------------------------ Manko-Novikov
+template <class T>
+struct MNPot {
+    D3<T> invf, F, om, G, Delta;
+};
+
+template <class T>
+GT_HD void mn_potentials(const SpacetimeC &c, T r, T th, MNPot<T> &P)
+{
+    T s, cs;
+    sincos_t(th, &s, &cs);
+    const T ik = T(c.ik);
+    const T two_beta = T(c.two_beta);
+    const D3<T> x = {(r - T(c.M)) * ik, ik, T(0)};
+    const D3<T> xm1 = {(r - T(c.r_plus)) * ik, ik, T(0)}; // x - 1 without cancellation
+    const D3<T> xp1 = x + T(1);
+    const D3<T> y = {cs, T(0), -s};
+    const D3<T> s2 = {s * s, T(0), T(2) * s * cs}; // 1 - y^2
+    const D3<T> x2m1 = xm1 * xp1;
+    const D3<T> R2 = x2m1 + dsq(y); // x^2 + y^2 - 1
+    const D3<T> iR = drsqrt(R2);
+    const D3<T> u = x * y * iR; // Legendre argument x y / R
+    const D3<T> u2 = dsq(u);
+    const D3<T> P2 = u2 * T(1.5) - T(0.5);
+    const D3<T> P3 = u * (u2 * T(2.5) - T(1.5));
+    const D3<T> iR2 = dsq(iR);
+    const D3<T> iR3 = iR2 * iR;
+    const D3<T> uR2 = u * iR2, P2R3 = P2 * iR3;
+    // sum_l (+-1) P_l / R^{l+1} with the sign patterns of fraktur a, fraktur b, gamma'
+    const D3<T> Sa = (x - y) * (iR + uR2 + P2R3);
+    const D3<T> Sb = (x + y) * (uR2 - iR - P2R3);
+    const D3<T> Sg = T(2) * (x * iR - y * uR2 + x * P2R3);
+    const D3<T> fa = dexp((Sa - T(1)) * (-two_beta)) * T(-c.alpha);
+    const D3<T> fb = dexp((Sb + T(1)) * two_beta) * T(c.alpha);
+    const D3<T> ab = fa * fb;
+    const D3<T> opab = ab + T(1);
+    const D3<T> bma = fb - fa;
+    const D3<T> A = x2m1 * dsq(opab) - s2 * dsq(bma);
+    const D3<T> B = dsq(xp1 + xm1 * ab) + dsq((y + T(1)) * fa + (T(1) - y) * fb);
+    const D3<T> C = x2m1 * opab * (bma - y * (fa + fb)) + s2 * bma * (opab + x * (T(1) - ab));
+    const D3<T> psi2 = P2R3 * two_beta;                                   // 2 psi
+    const D3<T> g2 = T(c.three_beta2) * dsq(iR3) * (dsq(P3) - dsq(P2)) + (Sg - T(2)) * two_beta; // 2 gamma''
+    const D3<T> e2psi = dexp(psi2);
+    const D3<T> ie2psi = drcp(e2psi);
+    const D3<T> iA = drcp(A);
+    const D3<T> iB = drcp(B);
+    P.invf = ie2psi * B * iA;
+    P.F = e2psi * A * iB * drcp(x2m1 * s2) * T(1.0 / c.k2);
+    P.om = ie2psi * C * iA * T(c.two_k) - T(c.w_inf);
+    P.G = dexp(psi2 - g2) * iB * T(c.c_g);
+    P.Delta = x2m1 * T(c.k2);
+}
+
+template <class T>
+GT_HD void mn_rates(const SpacetimeC &c, T r, T th, T pr, T pth, T pt, T pph,
+                                         Rates<T> &o)
+{
+    MNPot<T> P;
+    mn_potentials(c, r, th, P);
+    const D3<T> pw = P.om * pt + pph;                 // p_phi + w p_t
+    const D3<T> H2 = P.invf * (-pt * pt) + P.F * dsq(pw) + P.G * (P.Delta * (pr * pr) + pth * pth);
+    const T Fpw = P.F.v * pw.v;
+    o.dt = fma_t(Fpw, P.om.v, -pt * P.invf.v);
+    o.dph = Fpw;
+    o.dr = P.G.v * P.Delta.v * pr;
+    o.dth = P.G.v * pth;
+    o.dpr = T(-0.5) * H2.r;
+    o.dpth = T(-0.5) * H2.t;
+}
+
+#ifdef __CUDACC__
+__device__ __forceinline__ void mn_upper(const SpacetimeC &c, double r, double th, double g[5])
+{
+    MNPot<double> P;
+    mn_potentials(c, r, th, P);
+    g[0] = -P.invf.v + P.om.v * P.om.v * P.F.v;
+    g[1] = P.om.v * P.F.v;
+    g[2] = P.F.v;
+    g[3] = P.G.v * P.Delta.v;
+    g[4] = P.G.v;
+}
+
+template <int KIND, class T>
+GT_HD void rates(const SpacetimeC &c, T r, T th, T pr, T pth, T pt, T pph,
+                                      Rates<T> &o)
+{
+    if (KIND == KIND_KERR)
+        kerr_rates<T>(c, r, th, pr, pth, pt, pph, o);
+    else
+        mn_rates<T>(c, r, th, pr, pth, pt, pph, o);
+}
+
+__device__ __forceinline__ void upper_metric(const SpacetimeC &c, double r, double th, double g[5])
+{
+    if (c.kind == KIND_KERR)
+        kerr_upper(c, r, th, g);
+    else
+        mn_upper(c, r, th, g);
+}
+#endif
+
+} // namespace gt

@@ -1,0 +1,540 @@
+// trace.cu -- camera set-up and the persistent RK4 ray-queue kernels (sm_103a).
+//
+// One lane integrates one ray.  In the persistent form a grid of a few blocks per
+// SM loops until the global ray queue is empty: whenever lanes of a warp finish,
+// the warp counts them with __ballot_sync, one elected lane claims that many new
+// ray ids with a single atomicAdd, and the lanes rebuild their initial data from
+// the pixel index (camera initialisation is fused -- there are no input arrays).
+// Rays that stop early (horizon) therefore do not leave their lanes idle.  Every
+// ray runs the same instruction sequence whatever lane, warp or launch shape it
+// lands in, so results are bitwise independent of the launch configuration.
+//
+// Method (Sec. 3.1.2 RK4; appendix listing's propagation kernel for the step rule
+// and exit tests):
+//   k1 = F(x);  h = |sp / k1.q^t|;  k2 = F(x + h/2 k1);  k3 = F(x + h/2 k2);
+//   k4 = F(x + h k3);  x += h w (k1 + 2 k2 + 2 k3 + k4),  w = 1/6 (0.1667 compat);
+//   then r > 1.5 r0 -> ESCAPED, else h < sp 3e-5 -> HORIZON, else n_steps -> MAXSTEPS;
+//   a non-finite step -> NONFINITE keeping the last finite state.
+// Only (r, theta, p_r, p_theta) enter F; t and phi are quadratures and p_t, p_phi
+// are constants of motion, so the state is 6 evolving numbers plus 2 constants.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "../../include/geotrace.h"
+#include "internal.cuh"
+#include "spacetime.cuh"
+
+namespace gt {
+
+#define FULL_MASK 0xffffffffu
+
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ------------------------------------------------------------------ camera set-up
+// Spacetime constants (Sec. 2.2.2: a = S/M; Sec. 2.2.3: alpha, k, beta), the pixel
+// ranges V = tan(FOV/2)/r0 and H = atan(tan(V) res_x/res_y) of the listing, and the
+// lower metric at the camera (inverse of g^{mu nu}'s (t, phi) block and diagonal).
+__global__ void camera_setup_kernel(CamDesc *cams, int n, int flags, double r_switch)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    CamDesc d = cams[c];
+    SpacetimeC st = {};
+    st.M = d.M;
+    if (d.Q != 0.0) {
+        st.kind = KIND_MN;
+        const double sm = d.S / d.M;
+        const double al = (-d.M + sqrt(d.M * d.M - sm * sm)) / sm;
+        const double k = d.M * (1.0 - al * al) / (1.0 + al * al);
+        st.alpha = al;
+        st.k = k;
+        st.ik = 1.0 / k;
+        st.beta = d.Q * d.M * d.M * d.M / (k * k * k);
+        st.two_beta = 2.0 * st.beta;
+        st.three_beta2 = 3.0 * st.beta * st.beta;
+        st.c_g = (1.0 - al * al) * (1.0 - al * al) / (k * k);
+        st.w_inf = 4.0 * k * al / (1.0 - al * al);
+        st.k2 = k * k;
+        st.two_k = 2.0 * k;
+        st.r_plus = d.M + k;
+    } else {
+        st.kind = KIND_KERR;
+        st.a = d.S / d.M;
+        st.a2 = st.a * st.a;
+        st.r_plus = d.M + sqrt(d.M * d.M - st.a2);
+    }
+    d.st = st;
+    d.V = tan(0.5 * d.fov_deg / 180.0 * M_PI) / d.r0;
+    d.H = atan(tan(d.V) * (double)d.res_x / (double)d.res_y);
+    d.inv_sin_th0 = (flags & GT_FLAG_COMPAT_CAMERA) ? 1.0 : 1.0 / sin(d.th0);
+    double g[5];
+    upper_metric(st, d.r0, d.th0, g);
+    const double det = g[0] * g[2] - g[1] * g[1];
+    d.gl_tt = g[2] / det;
+    d.gl_tph = -g[1] / det;
+    d.gl_phph = g[0] / det;
+    d.gl_rr = 1.0 / g[3];
+    d.gl_thth = 1.0 / g[4];
+    d.r_escape = 1.5 * d.r0;
+    if (r_switch > 0.0) {
+        d.r_switch = r_switch;
+    } else if (r_switch < 0.0) {
+        d.r_switch = 0.0;
+    } else if (st.kind == KIND_KERR) {
+        // 1.5 x the outermost (retrograde) circular photon orbit of Kerr
+        const double chi = fmin(fabs(st.a) / d.M, 1.0);
+        const double r_ph = 2.0 * d.M * (1.0 + cos(2.0 / 3.0 * acos(chi)));
+        d.r_switch = 1.5 * r_ph;
+    } else {
+        d.r_switch = 4.0 * d.M;
+    }
+    d.valid = (d.gl_tt < 0.0 && isfinite(d.gl_tt) && isfinite(d.gl_phph) && isfinite(d.gl_rr) &&
+               isfinite(d.gl_thth) && d.gl_rr > 0.0 && d.gl_thth > 0.0)
+                  ? 1
+                  : 0;
+    cams[c] = d;
+}
+
+cudaError_t launch_camera_setup(CamDesc *d_cams, int n_cams, int flags, double r_switch,
+                                cudaStream_t s)
+{
+    const int block = 64;
+    camera_setup_kernel<<<(n_cams + block - 1) / block, block, 0, s>>>(d_cams, n_cams, flags,
+                                                                       r_switch);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ ray state
+struct Ray64 {
+    double t, r, th, ph, pr, pth; // evolving
+    double pt, pph;               // constants of motion
+};
+
+// Initial data of pixel `local` of camera `c` (Sec. 3.3.1, listing's camera block):
+// v = (T, -1, beta_j, alpha_i / sin theta0), T the root (-B + sqrt(B^2 - 4AC))/(2A)
+// of g(v, v) = 0, v /= |T|, p = g v at (0, r0, theta0, 0).
+__device__ __forceinline__ void camera_init(const CamDesc &c, int64_t local, Ray64 &x)
+{
+    const int i = (int)(local % c.res_x);
+    const int j = (int)(local / c.res_x);
+    const double al = c.res_x > 1 ? c.H * (double)(2 * i - (c.res_x - 1)) / (double)(c.res_x - 1) : 0.0;
+    const double bt = c.res_y > 1 ? c.V * (double)(2 * j - (c.res_y - 1)) / (double)(c.res_y - 1) : 0.0;
+    double vr = -1.0, vth = bt, vph = al * c.inv_sin_th0;
+    const double A = c.gl_tt;
+    const double B = 2.0 * c.gl_tph * vph;
+    const double C = c.gl_rr * vr * vr + c.gl_thth * vth * vth + c.gl_phph * vph * vph;
+    const double T = (-B + sqrt(B * B - 4.0 * A * C)) / (2.0 * A);
+    const double sc = 1.0 / fabs(T);
+    const double vt = T * sc;
+    vr *= sc;
+    vth *= sc;
+    vph *= sc;
+    x.t = 0.0;
+    x.r = c.r0;
+    x.th = c.th0;
+    x.ph = 0.0;
+    x.pt = c.gl_tt * vt + c.gl_tph * vph;
+    x.pr = c.gl_rr * vr;
+    x.pth = c.gl_thth * vth;
+    x.pph = c.gl_tph * vt + c.gl_phph * vph;
+}
+
+template <int KIND>
+__device__ __forceinline__ void rates_any(const SpacetimeC &st, double r, double th, double pr,
+                                          double pth, double pt, double pph, Rates<double> &o)
+{
+    if (KIND == 2) {
+        if (st.kind == KIND_KERR)
+            kerr_rates<double>(st, r, th, pr, pth, pt, pph, o);
+        else
+            mn_rates<double>(st, r, th, pr, pth, pt, pph, o);
+    } else {
+        rates<KIND, double>(st, r, th, pr, pth, pt, pph, o);
+    }
+}
+
+// One FP64 RK4 step; returns h and writes the candidate state to y.
+template <int KIND>
+__device__ __forceinline__ double rk4_step64(const SpacetimeC &st, const Ray64 &x, double sp,
+                                             double w6, Ray64 &y)
+{
+    Rates<double> k1, k2, k3, k4;
+    rates_any<KIND>(st, x.r, x.th, x.pr, x.pth, x.pt, x.pph, k1);
+    const double h = fabs(sp / k1.dt);
+    const double hh = 0.5 * h;
+    rates_any<KIND>(st, x.r + hh * k1.dr, x.th + hh * k1.dth, x.pr + hh * k1.dpr,
+                    x.pth + hh * k1.dpth, x.pt, x.pph, k2);
+    rates_any<KIND>(st, x.r + hh * k2.dr, x.th + hh * k2.dth, x.pr + hh * k2.dpr,
+                    x.pth + hh * k2.dpth, x.pt, x.pph, k3);
+    rates_any<KIND>(st, x.r + h * k3.dr, x.th + h * k3.dth, x.pr + h * k3.dpr,
+                    x.pth + h * k3.dpth, x.pt, x.pph, k4);
+    const double hw = h * w6;
+    y.t = x.t + hw * (k1.dt + 2.0 * k2.dt + 2.0 * k3.dt + k4.dt);
+    y.r = x.r + hw * (k1.dr + 2.0 * k2.dr + 2.0 * k3.dr + k4.dr);
+    y.th = x.th + hw * (k1.dth + 2.0 * k2.dth + 2.0 * k3.dth + k4.dth);
+    y.ph = x.ph + hw * (k1.dph + 2.0 * k2.dph + 2.0 * k3.dph + k4.dph);
+    y.pr = x.pr + hw * (k1.dpr + 2.0 * k2.dpr + 2.0 * k3.dpr + k4.dpr);
+    y.pth = x.pth + hw * (k1.dpth + 2.0 * k2.dpth + 2.0 * k3.dpth + k4.dpth);
+    y.pt = x.pt;
+    y.pph = x.pph;
+    return h;
+}
+
+__device__ __forceinline__ bool finite6(const Ray64 &y)
+{
+    return isfinite(y.t) && isfinite(y.r) && isfinite(y.th) && isfinite(y.ph) && isfinite(y.pr) &&
+           isfinite(y.pth);
+}
+
+__device__ __forceinline__ void store_ray(const TraceArgs &A, int64_t id, double t, double r,
+                                          double th, double ph, int status, uint32_t n)
+{
+    if (A.t) A.t[id] = t;
+    if (A.r) A.r[id] = r;
+    if (A.th) A.th[id] = th;
+    if (A.ph) A.ph[id] = ph;
+    if (A.status) A.status[id] = (uint8_t)status;
+    if (A.nsteps) A.nsteps[id] = n;
+}
+
+// Camera of flat ray id (binary search over the prefix offsets).
+__device__ __forceinline__ int find_camera(const CamDesc *__restrict__ cams, int n_cams, int64_t id)
+{
+    int lo = 0, hi = n_cams - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cams[mid].offset <= id)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Status after a step (listing's order: escape first, then step collapse).
+__device__ __forceinline__ int exit_status(double r, double h, double r_esc, double sp, uint32_t n,
+                                           int64_t n_steps)
+{
+    if (r > r_esc) return GT_RAY_ESCAPED;
+    if (h < sp * 0.00003) return GT_RAY_HORIZON;
+    if ((int64_t)n >= n_steps) return GT_RAY_MAXSTEPS;
+    return -1;
+}
+
+// ------------------------------------------------------------------ FP32-mixed pieces
+// Compensated (hi, lo) float pair: x = hi + lo with |lo| <= ulp(hi)/2.
+struct F2 {
+    float hi, lo;
+};
+__device__ __forceinline__ F2 f2_from(double v)
+{
+    const float h = (float)v;
+    return {h, (float)(v - (double)h)};
+}
+__device__ __forceinline__ double f2_to(F2 a) { return (double)a.hi + (double)a.lo; }
+// a += d with an error-free TwoSum, then renormalise.
+__device__ __forceinline__ void f2_add(F2 &a, float d)
+{
+    const float s = a.hi + d;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (d - bb);
+    const float lo = a.lo + e;
+    const float s2 = s + lo;
+    a.lo = lo - (s2 - s);
+    a.hi = s2;
+}
+
+struct RayMixed {
+    F2 t, r, th, ph, pr, pth;
+    double pt, pph; // constants of motion kept in FP64
+    float ptf, pphf;
+};
+
+__device__ __forceinline__ void mixed_from64(const Ray64 &x, RayMixed &m)
+{
+    m.t = f2_from(x.t);
+    m.r = f2_from(x.r);
+    m.th = f2_from(x.th);
+    m.ph = f2_from(x.ph);
+    m.pr = f2_from(x.pr);
+    m.pth = f2_from(x.pth);
+    m.pt = x.pt;
+    m.pph = x.pph;
+    m.ptf = (float)x.pt;
+    m.pphf = (float)x.pph;
+}
+
+__device__ __forceinline__ void mixed_to64(const RayMixed &m, Ray64 &x)
+{
+    x.t = f2_to(m.t);
+    x.r = f2_to(m.r);
+    x.th = f2_to(m.th);
+    x.ph = f2_to(m.ph);
+    x.pr = f2_to(m.pr);
+    x.pth = f2_to(m.pth);
+    x.pt = m.pt;
+    x.pph = m.pph;
+}
+
+template <int KIND>
+__device__ __forceinline__ void rates_f32(const SpacetimeC &st, float r, float th, float pr,
+                                          float pth, float pt, float pph, Rates<float> &o)
+{
+    if (KIND == 2) {
+        if (st.kind == KIND_KERR)
+            kerr_rates<float>(st, r, th, pr, pth, pt, pph, o);
+        else
+            mn_rates<float>(st, r, th, pr, pth, pt, pph, o);
+    } else {
+        rates<KIND, float>(st, r, th, pr, pth, pt, pph, o);
+    }
+}
+
+// One FP32 RK4 step on the compensated state; returns h (as float).
+template <int KIND>
+__device__ __forceinline__ float rk4_step32(const SpacetimeC &st, RayMixed &m, float sp, float w6)
+{
+    Rates<float> k1, k2, k3, k4;
+    const float r = m.r.hi, th = m.th.hi, pr = m.pr.hi, pth = m.pth.hi;
+    rates_f32<KIND>(st, r, th, pr, pth, m.ptf, m.pphf, k1);
+    const float h = fabsf(sp / k1.dt);
+    const float hh = 0.5f * h;
+    rates_f32<KIND>(st, fmaf(hh, k1.dr, r), fmaf(hh, k1.dth, th), fmaf(hh, k1.dpr, pr),
+                    fmaf(hh, k1.dpth, pth), m.ptf, m.pphf, k2);
+    rates_f32<KIND>(st, fmaf(hh, k2.dr, r), fmaf(hh, k2.dth, th), fmaf(hh, k2.dpr, pr),
+                    fmaf(hh, k2.dpth, pth), m.ptf, m.pphf, k3);
+    rates_f32<KIND>(st, fmaf(h, k3.dr, r), fmaf(h, k3.dth, th), fmaf(h, k3.dpr, pr),
+                    fmaf(h, k3.dpth, pth), m.ptf, m.pphf, k4);
+    const float hw = h * w6;
+    f2_add(m.t, hw * (k1.dt + 2.0f * k2.dt + 2.0f * k3.dt + k4.dt));
+    f2_add(m.r, hw * (k1.dr + 2.0f * k2.dr + 2.0f * k3.dr + k4.dr));
+    f2_add(m.th, hw * (k1.dth + 2.0f * k2.dth + 2.0f * k3.dth + k4.dth));
+    f2_add(m.ph, hw * (k1.dph + 2.0f * k2.dph + 2.0f * k3.dph + k4.dph));
+    f2_add(m.pr, hw * (k1.dpr + 2.0f * k2.dpr + 2.0f * k3.dpr + k4.dpr));
+    f2_add(m.pth, hw * (k1.dpth + 2.0f * k2.dpth + 2.0f * k3.dpth + k4.dpth));
+    return h;
+}
+
+// H = 0 re-projection in FP64 (mixed mode): solve g^rr p_r^2 = -(rest) for |p_r|,
+// keeping the sign of p_r.  Skipped near radial turning points, where the radial
+// term is small against the rest and the square root is ill-conditioned.
+__device__ __forceinline__ void reproject_pr(const SpacetimeC &st, Ray64 &x)
+{
+    double g[5];
+    upper_metric(st, x.r, x.th, g);
+    const double rest = g[0] * x.pt * x.pt + 2.0 * g[1] * x.pt * x.pph + g[2] * x.pph * x.pph +
+                        g[4] * x.pth * x.pth;
+    const double rad = g[3] * x.pr * x.pr;
+    const double scale = fabs(g[0] * x.pt * x.pt) + fabs(g[2] * x.pph * x.pph) + rad +
+                         g[4] * x.pth * x.pth;
+    if (!(rad > 0.05 * scale)) return;
+    const double pr2 = -rest / g[3];
+    if (!(pr2 > 0.0) || !isfinite(pr2)) return;
+    x.pr = copysign(sqrt(pr2), x.pr);
+}
+
+// ------------------------------------------------------------------ the kernel
+// MODE 0: FP64 plain.  MODE 1: FP32-mixed.  KIND: 0 Kerr, 1 MN, 2 per-camera.
+template <int MODE, int KIND>
+__global__ void __launch_bounds__(256) trace_kernel(TraceArgs A, int one_shot)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    unsigned long long *next = A.scratch + SCR_NEXT_RAY;
+    volatile unsigned long long *tflag = A.scratch + SCR_TIMEOUT;
+    const uint64_t t_start = A.timeout_ns ? globaltimer_ns() : 0;
+    const CamDesc *__restrict__ cams = A.cams;
+
+    int64_t id = -1;
+    int cam = 0;
+    bool active = false;
+    bool drained = false;
+    uint32_t n = 0;
+    Ray64 x;
+    RayMixed m;
+    SpacetimeC st = cams[0].st;
+    double r_esc = cams[0].r_escape;
+    double r_sw = cams[0].r_switch;
+    const float spf = (float)A.sp, w6f = (float)A.w6;
+
+    // Start ray `rid`; returns false (ray already written) when n_steps == 0.
+    auto start = [&](int64_t rid) -> bool {
+        id = rid;
+        if (KIND == 2 || A.n_cams > 1) {
+            cam = find_camera(cams, A.n_cams, rid);
+            st = cams[cam].st;
+            r_esc = cams[cam].r_escape;
+            r_sw = cams[cam].r_switch;
+        }
+        camera_init(cams[cam], A.first + rid - cams[cam].offset, x);
+        n = 0;
+        if (A.n_steps <= 0) {
+            store_ray(A, rid, x.t, x.r, x.th, x.ph, GT_RAY_MAXSTEPS, 0);
+            return false;
+        }
+        if (MODE == 1) mixed_from64(x, m);
+        return true;
+    };
+
+    if (one_shot) {
+        drained = true;
+        const int64_t rid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        if (rid < A.n_rays) active = start(rid);
+    }
+
+    for (uint32_t it = 0;; ++it) {
+        // ---- refill finished lanes from the global queue
+        if (!drained) {
+            const unsigned need = __ballot_sync(FULL_MASK, !active);
+            if (need) {
+                const int cnt = __popc(need);
+                const int leader = __ffs(need) - 1;
+                unsigned long long base = 0;
+                if (lane == leader) base = atomicAdd(next, (unsigned long long)cnt);
+                base = __shfl_sync(FULL_MASK, base, leader);
+                if (base + (unsigned long long)cnt >= (unsigned long long)A.n_rays) drained = true;
+                if (!active) {
+                    const int64_t rid = (int64_t)base + __popc(need & lt_mask);
+                    if (rid < A.n_rays) active = start(rid);
+                }
+            }
+        }
+        if (!__any_sync(FULL_MASK, active)) {
+            if (drained) break;
+            continue;
+        }
+        // ---- watchdog: stop every lane with status TIMEOUT
+        if (A.timeout_ns && (it & 127u) == 0u) {
+            int stop = 0;
+            if (lane == 0) {
+                if (*tflag) {
+                    stop = 1;
+                } else if (globaltimer_ns() - t_start > A.timeout_ns) {
+                    atomicExch(A.scratch + SCR_TIMEOUT, 1ull);
+                    stop = 1;
+                }
+            }
+            stop = __shfl_sync(FULL_MASK, stop, 0);
+            if (stop) {
+                if (active) {
+                    if (MODE == 1) mixed_to64(m, x);
+                    store_ray(A, id, x.t, x.r, x.th, x.ph, GT_RAY_TIMEOUT, n);
+                }
+                if (!one_shot) {
+                    for (;;) { // drain the queue without integrating
+                        unsigned long long base = 0;
+                        if (lane == 0) base = atomicAdd(next, 32ull);
+                        base = __shfl_sync(FULL_MASK, base, 0);
+                        if (base >= (unsigned long long)A.n_rays) break;
+                        const int64_t rid = (int64_t)base + lane;
+                        if (rid < A.n_rays) {
+                            const int c = A.n_cams > 1 ? find_camera(cams, A.n_cams, rid) : 0;
+                            store_ray(A, rid, 0.0, cams[c].r0, cams[c].th0, 0.0, GT_RAY_TIMEOUT, 0);
+                        }
+                    }
+                }
+                return;
+            }
+        }
+        if (!active) continue;
+
+        // ---- one RK4 step
+        int status = -1;
+        if (MODE == 0) {
+            Ray64 y;
+            const double h = rk4_step64<KIND>(st, x, A.sp, A.w6, y);
+            ++n;
+            if (!isfinite(h) || !finite6(y)) {
+                status = GT_RAY_NONFINITE;
+            } else {
+                x = y;
+                status = exit_status(x.r, h, r_esc, A.sp, n, A.n_steps);
+            }
+        } else {
+            double h;
+            bool ok = true;
+            if ((double)m.r.hi < r_sw) { // FP64 zone (near the horizon / photon orbits)
+                Ray64 y;
+                mixed_to64(m, x);
+                h = rk4_step64<KIND>(st, x, A.sp, A.w6, y);
+                ok = isfinite(h) && finite6(y);
+                if (ok) mixed_from64(y, m);
+            } else {
+                RayMixed keep = m;
+                h = (double)rk4_step32<KIND>(st, m, spf, w6f);
+                ok = isfinite(h) && isfinite(m.t.hi) && isfinite(m.r.hi) && isfinite(m.th.hi) &&
+                     isfinite(m.ph.hi) && isfinite(m.pr.hi) && isfinite(m.pth.hi);
+                if (!ok) m = keep;
+            }
+            ++n;
+            if (!ok) {
+                status = GT_RAY_NONFINITE;
+                mixed_to64(m, x);
+            } else {
+                const double r_now = f2_to(m.r);
+                status = exit_status(r_now, h, r_esc, A.sp, n, A.n_steps);
+                if (status >= 0) {
+                    mixed_to64(m, x);
+                } else if (A.reproject_every > 0 && (n % (uint32_t)A.reproject_every) == 0u) {
+                    mixed_to64(m, x);
+                    reproject_pr(st, x);
+                    m.pr = f2_from(x.pr);
+                }
+            }
+        }
+        if (status >= 0) {
+            store_ray(A, id, x.t, x.r, x.th, x.ph, status, n);
+            active = false;
+        }
+    }
+}
+
+template <int MODE, int KIND>
+static cudaError_t launch_one(const TraceArgs &a, int block, int grid, bool one_shot, cudaStream_t s)
+{
+    trace_kernel<MODE, KIND><<<grid, block, 0, s>>>(a, one_shot ? 1 : 0);
+    return cudaGetLastError();
+}
+
+template <int MODE, int KIND>
+static int occupancy_one(int block)
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, trace_kernel<MODE, KIND>, block, 0) !=
+        cudaSuccess)
+        return 1;
+    return n > 0 ? n : 1;
+}
+
+int max_blocks_per_sm(int mode, int kind_hint, int block)
+{
+    if (mode == GT_MODE_FP64) {
+        if (kind_hint == KIND_KERR) return occupancy_one<0, KIND_KERR>(block);
+        if (kind_hint == KIND_MN) return occupancy_one<0, KIND_MN>(block);
+        return occupancy_one<0, 2>(block);
+    }
+    if (kind_hint == KIND_KERR) return occupancy_one<1, KIND_KERR>(block);
+    if (kind_hint == KIND_MN) return occupancy_one<1, KIND_MN>(block);
+    return occupancy_one<1, 2>(block);
+}
+
+cudaError_t launch_trace(const TraceArgs &a, int mode, int kind_hint, int block, int grid,
+                         bool one_shot, cudaStream_t s)
+{
+    if (mode == GT_MODE_FP64) {
+        if (kind_hint == KIND_KERR) return launch_one<0, KIND_KERR>(a, block, grid, one_shot, s);
+        if (kind_hint == KIND_MN) return launch_one<0, KIND_MN>(a, block, grid, one_shot, s);
+        return launch_one<0, 2>(a, block, grid, one_shot, s);
+    }
+    if (kind_hint == KIND_KERR) return launch_one<1, KIND_KERR>(a, block, grid, one_shot, s);
+    if (kind_hint == KIND_MN) return launch_one<1, KIND_MN>(a, block, grid, one_shot, s);
+    return launch_one<1, 2>(a, block, grid, one_shot, s);
+}
+
+} // namespace gt

@@ -1,0 +1,218 @@
+"""Thin Python binding of libgeotrace.so (include/geotrace.h) -- argument marshalling only.
+
+PyTorch supplies device memory and the CUDA stream; every step of the ray tracing
+runs in the library's CUDA kernels.  The binding never falls back to any other
+implementation: if the compiled library is missing or the device is not sm_103 it
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgeotrace.so")
+
+GT_OK = 0
+ERRORS = {-1: "invalid argument", -2: "not configured", -3: "CUDA error", -4: "out of memory",
+          -5: "device watchdog timeout", -6: "unsupported device or feature"}
+ESCAPED, HORIZON, MAXSTEPS, NONFINITE, TIMEOUT = 0, 1, 2, 3, 4
+MODE_FP64, MODE_FP32_MIXED = 0, 1
+FLAG_COMPAT_WEIGHTS, FLAG_COMPAT_CAMERA, FLAG_ONE_SHOT = 1, 2, 4
+
+# every symbol include/geotrace.h declares
+EXPORTS = ("gt_create", "gt_destroy", "gt_set_stream", "gt_set_spacetime", "gt_set_camera",
+           "gt_set_options", "gt_trace", "gt_trace_range", "gt_trace_host", "gt_trace_batch", "gt_sync",
+           "gt_device_sm_count", "gt_measure_fma_peak", "gt_strerror")
+
+
+class GeotraceError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {ERRORS.get(code, 'error')} (code {code})")
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("block_size", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
+                ("flags", ctypes.c_int), ("reproject_every", ctypes.c_int),
+                ("r_switch", ctypes.c_double), ("timeout_seconds", ctypes.c_double)]
+
+
+class CameraDesc(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_double), ("S", ctypes.c_double), ("Q", ctypes.c_double),
+                ("r0", ctypes.c_double), ("theta0", ctypes.c_double),
+                ("fov_deg", ctypes.c_double), ("res_x", ctypes.c_int32),
+                ("res_y", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libgeotrace.so; raises if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(
+            "libgeotrace.so is not built; run paper_2310_15183_gb300.build.build() (needs nvcc)")
+    lib = ctypes.CDLL(path)
+    vp, i, d, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    lib.gt_create.argtypes = [ctypes.POINTER(vp), i, vp]
+    lib.gt_destroy.argtypes = [vp]
+    lib.gt_set_stream.argtypes = [vp, vp]
+    lib.gt_set_spacetime.argtypes = [vp, d, d, d]
+    lib.gt_set_camera.argtypes = [vp, d, d, d, i, i]
+    lib.gt_set_options.argtypes = [vp, ctypes.POINTER(Options)]
+    out6 = [vp] * 6
+    lib.gt_trace.argtypes = [vp, i64, d, i] + out6
+    lib.gt_trace_range.argtypes = [vp, i64, i64, i64, d, i] + out6
+    lib.gt_trace_host.argtypes = [vp, i64, d, i] + out6
+    lib.gt_trace_batch.argtypes = [vp, ctypes.POINTER(CameraDesc), i, i64, d, i] + out6
+    lib.gt_sync.argtypes = [vp]
+    lib.gt_device_sm_count.argtypes = [vp, ctypes.POINTER(i)]
+    lib.gt_measure_fma_peak.argtypes = [i, i, i, ctypes.POINTER(d)]
+    lib.gt_strerror.argtypes = [i]
+    lib.gt_strerror.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name != "gt_strerror":
+            getattr(lib, name).restype = i
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, what: str):
+    if rc != GT_OK:
+        raise GeotraceError(rc, what)
+
+
+def _ptr(x) -> Optional[int]:
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def measure_fma_peak(device: int = 0, fp64: bool = True, iters: int = 2000) -> float:
+    """FLOP/s of independent FMA chains on `device` (gt_measure_fma_peak)."""
+    v = ctypes.c_double()
+    _check(load_library().gt_measure_fma_peak(device, 1 if fp64 else 0, iters, ctypes.byref(v)),
+           "gt_measure_fma_peak")
+    return v.value
+
+
+class Tracer:
+    """One library context (gt_ctx) on one CUDA device and stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        self._torch = torch
+        self.lib = load_library()
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.device = device
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _check(self.lib.gt_create(ctypes.byref(h), device, ctypes.c_void_p(stream.cuda_stream)),
+               "gt_create")
+        self.ctx = h
+        self.res = (0, 0)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.gt_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sm_count(self) -> int:
+        n = ctypes.c_int()
+        _check(self.lib.gt_device_sm_count(self.ctx, ctypes.byref(n)), "gt_device_sm_count")
+        return n.value
+
+    def set_spacetime(self, M: float, S: float, Q: float):
+        _check(self.lib.gt_set_spacetime(self.ctx, M, S, Q), "gt_set_spacetime")
+
+    def set_camera(self, r0: float, theta0: float, fov_deg: float, res_x: int, res_y: int):
+        _check(self.lib.gt_set_camera(self.ctx, r0, theta0, fov_deg, res_x, res_y),
+               "gt_set_camera")
+        self.res = (res_x, res_y)
+
+    def set_options(self, block_size=0, blocks_per_sm=0, flags=0, reproject_every=0,
+                    r_switch=0.0, timeout_seconds=0.0):
+        o = Options(block_size, blocks_per_sm, flags, reproject_every, r_switch, timeout_seconds)
+        _check(self.lib.gt_set_options(self.ctx, ctypes.byref(o)), "gt_set_options")
+
+    def alloc_outputs(self, n: int) -> dict:
+        torch = self._torch
+        dev = torch.device("cuda", self.device)
+        out = {k: torch.empty(n, dtype=torch.float64, device=dev) for k in ("t", "r", "th", "ph")}
+        out["status"] = torch.empty(n, dtype=torch.uint8, device=dev)
+        out["nsteps"] = torch.empty(n, dtype=torch.int32, device=dev)  # read as uint32
+        return out
+
+    def trace(self, n_steps: int, step_precision: float, mode: int = MODE_FP64,
+              out: Optional[dict] = None) -> dict:
+        """gt_trace into device tensors (allocated here when `out` is None)."""
+        n = self.res[0] * self.res[1]
+        if out is None:
+            out = self.alloc_outputs(n)
+        rc = self.lib.gt_trace(self.ctx, int(n_steps), float(step_precision), int(mode),
+                               *[_ptr(out.get(k)) for k in ("t", "r", "th", "ph", "status",
+                                                             "nsteps")])
+        _check(rc, "gt_trace")
+        return out
+
+    def trace_range(self, first: int, count: int, n_steps: int, step_precision: float,
+                    mode: int = MODE_FP64, out: Optional[dict] = None) -> dict:
+        """gt_trace_range: pixels [first, first + count) into device tensors."""
+        if out is None:
+            out = self.alloc_outputs(count)
+        rc = self.lib.gt_trace_range(self.ctx, int(first), int(count), int(n_steps),
+                                     float(step_precision), int(mode),
+                                     *[_ptr(out.get(k)) for k in ("t", "r", "th", "ph",
+                                                                   "status", "nsteps")])
+        _check(rc, "gt_trace_range")
+        return out
+
+    def trace_host(self, n_steps: int, step_precision: float, mode: int = MODE_FP64,
+                   out: Optional[dict] = None) -> dict:
+        """gt_trace_host into host (numpy or pinned torch) arrays."""
+        n = self.res[0] * self.res[1]
+        if out is None:
+            out = {k: np.empty(n) for k in ("t", "r", "th", "ph")}
+            out["status"] = np.empty(n, dtype=np.uint8)
+            out["nsteps"] = np.empty(n, dtype=np.uint32)
+        rc = self.lib.gt_trace_host(self.ctx, int(n_steps), float(step_precision), int(mode),
+                                    *[_ptr(out.get(k)) for k in ("t", "r", "th", "ph",
+                                                                  "status", "nsteps")])
+        _check(rc, "gt_trace_host")
+        return out
+
+    def trace_batch(self, cams: Sequence, n_steps: int, step_precision: float,
+                    mode: int = MODE_FP64, out: Optional[dict] = None) -> dict:
+        """gt_trace_batch over camera objects with M, S, Q, r0, theta0, fov_deg, res_x, res_y."""
+        arr = (CameraDesc * len(cams))()
+        total = 0
+        for k, c in enumerate(cams):
+            arr[k] = CameraDesc(c.M, c.S, c.Q, c.r0, c.theta0, c.fov_deg, c.res_x, c.res_y)
+            total += c.res_x * c.res_y
+        if out is None:
+            out = self.alloc_outputs(total)
+        rc = self.lib.gt_trace_batch(self.ctx, arr, len(cams), int(n_steps),
+                                     float(step_precision), int(mode),
+                                     *[_ptr(out.get(k)) for k in ("t", "r", "th", "ph",
+                                                                   "status", "nsteps")])
+        _check(rc, "gt_trace_batch")
+        return out
+
+    def sync(self):
+        _check(self.lib.gt_sync(self.ctx), "gt_sync")

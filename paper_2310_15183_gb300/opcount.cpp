@@ -1,0 +1,90 @@
+// opcount.cpp -- algorithmic operation count of one RK4 step, taken from the very
+// templates the kernels run (spacetime.cuh) instantiated with a counting scalar.
+// Host-only program; prints JSON.  Convention: add, sub, mul = 1 flop, fma = 2,
+// div, rsqrt, exp = 1 each, sincos = 2 (sin and cos); negation is free.
+#include <math.h>
+#include <stdio.h>
+
+struct Counts {
+    long add = 0, mul = 0, fma = 0, div = 0, rsqrt = 0, exp = 0, sincos = 0;
+};
+
+static Counts g_c;
+
+struct CN {
+    double v;
+    CN(double x = 0.0) : v(x) {}
+};
+static CN operator+(CN a, CN b) { g_c.add++; return CN(a.v + b.v); }
+static CN operator-(CN a, CN b) { g_c.add++; return CN(a.v - b.v); }
+static CN operator*(CN a, CN b) { g_c.mul++; return CN(a.v * b.v); }
+static CN operator/(CN a, CN b) { g_c.div++; return CN(a.v / b.v); }
+static CN operator-(CN a) { return CN(-a.v); }
+
+// found by argument-dependent lookup from the templates in namespace gt
+static void sincos_t(CN x, CN *s, CN *c) { g_c.sincos++; *s = CN(sin(x.v)); *c = CN(cos(x.v)); }
+static CN exp_t(CN x) { g_c.exp++; return CN(exp(x.v)); }
+static CN rsqrt_t(CN x) { g_c.rsqrt++; return CN(1.0 / sqrt(x.v)); }
+static CN fma_t(CN a, CN b, CN c) { g_c.fma++; return CN(a.v * b.v + c.v); }
+
+#include "csrc/spacetime.cuh"
+
+static long flops(const Counts &c)
+{
+    return c.add + c.mul + 2 * c.fma + c.div + c.rsqrt + c.exp + 2 * c.sincos;
+}
+
+static void print_counts(const char *name, const Counts &c, bool last)
+{
+    printf("  \"%s\": {\"add\": %ld, \"mul\": %ld, \"fma\": %ld, \"div\": %ld, \"rsqrt\": %ld, "
+           "\"exp\": %ld, \"sincos\": %ld, \"flops\": %ld}%s\n",
+           name, c.add, c.mul, c.fma, c.div, c.rsqrt, c.exp, c.sincos, flops(c), last ? "" : ",");
+}
+
+int main()
+{
+    gt::SpacetimeC st = {};
+    st.M = 0.5;
+    st.a = 0.48;
+    st.a2 = st.a * st.a;
+    st.k = 0.14;
+    st.ik = 1.0 / st.k;
+    st.alpha = -0.75;
+    st.beta = 91.1;
+    st.two_beta = 2 * st.beta;
+    st.three_beta2 = 3 * st.beta * st.beta;
+    st.c_g = 1.0;
+    st.w_inf = 0.1;
+    st.k2 = st.k * st.k;
+    st.two_k = 2 * st.k;
+    st.r_plus = st.M + st.k;
+    gt::Rates<CN> o;
+    g_c = Counts();
+    gt::kerr_rates<CN>(st, CN(5.0), CN(1.1), CN(0.2), CN(0.3), CN(0.9), CN(-2.0), o);
+    const Counts kerr = g_c;
+    g_c = Counts();
+    gt::mn_rates<CN>(st, CN(5.0), CN(1.1), CN(0.2), CN(0.3), CN(0.9), CN(-2.0), o);
+    const Counts mn = g_c;
+    // RK4 combination outside the four field evaluations (trace.cu, rk4_step64):
+    //   h = |sp / k1.dt|: 1 div; hh = 0.5 h: 1 mul; 3 stages x 4 state fma;
+    //   hw = h w: 1 mul; 6 components x (k1 + 2k2 + 2k3 + k4: 2 fma + 1 add; x + hw s: 1 fma)
+    Counts comb;
+    comb.div = 1;
+    comb.mul = 2;
+    comb.fma = 12 + 6 * 3;
+    comb.add = 6;
+    // FP32-mixed adds a compensated TwoSum + renormalisation (10 adds) per component
+    Counts comp;
+    comp.add = 6 * 10;
+    printf("{\n");
+    print_counts("kerr_field", kerr, false);
+    print_counts("mn_field", mn, false);
+    print_counts("rk4_combination", comb, false);
+    print_counts("compensated_update", comp, false);
+    printf("  \"kerr_step_flops\": %ld,\n", 4 * flops(kerr) + flops(comb));
+    printf("  \"mn_step_flops\": %ld,\n", 4 * flops(mn) + flops(comb));
+    printf("  \"kerr_step_flops_mixed\": %ld,\n", 4 * flops(kerr) + flops(comb) + flops(comp));
+    printf("  \"mn_step_flops_mixed\": %ld\n", 4 * flops(mn) + flops(comb) + flops(comp));
+    printf("}\n");
+    return 0;
+}

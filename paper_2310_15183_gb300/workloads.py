@@ -61,6 +61,14 @@ WORKLOADS = {
 }
 
 
+# smaller cases of the same kernels, for profiler captures
+WORKLOADS["mn256"] = Workload("mn256", dataclasses.replace(MN_1000, res_x=256, res_y=256),
+                              20000, 1.5e-4)
+WORKLOADS["mn256_short"] = Workload("mn256_short",
+                                    dataclasses.replace(MN_1000, res_x=256, res_y=256),
+                                    2000, 1.5e-4)
+
+
 def sub_camera(cam: Camera, res_x: int, res_y: int) -> Camera:
     """Same spacetime and viewpoint at another resolution."""
     return dataclasses.replace(cam, res_x=res_x, res_y=res_y)

@@ -1,0 +1,277 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+FP64 plain must match element by element to 1e-9 relative (per component, scaled by
+max(1, |value|)) with identical status and step counts, outside a stated chaotic
+band; the FP32-mixed path must agree on >= 99.9 % of classifications with end-angle
+error <= 1e-3 rad.  Sizes keep the oracle to seconds while spanning several warps,
+blocks and a ragged tail.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2310_15183_gb300 import workloads as W
+
+from .parity import (assert_fp64_parity, mixed_report, neighbour_band, schwarzschild_band,
+                     to_numpy)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2310_15183_gb300 import build, geotrace
+    build.build()
+    return geotrace
+
+
+@pytest.fixture()
+def tracer(g):
+    t = g.Tracer(0)
+    yield t
+    t.close()
+
+
+def run_gpu(tracer, cam, n_steps, sp, mode=0, **opts):
+    tracer.set_spacetime(cam.M, cam.S, cam.Q)
+    tracer.set_camera(cam.r0, cam.theta0, cam.fov_deg, cam.res_x, cam.res_y)
+    tracer.set_options(**opts)
+    out = tracer.trace(n_steps, sp, mode)
+    torch.cuda.synchronize()
+    return to_numpy(out)
+
+
+def run_oracle(oracle, cam, n_steps, sp, pixels=None, flags=0, **kw):
+    return oracle.trace_image(cam.M, cam.S, cam.Q, cam.r0, cam.theta0, cam.fov_deg, cam.res_x,
+                              cam.res_y, n_steps, sp, flags=flags, pixels=pixels, **kw)
+
+
+SCHW = W.SCHW_64
+MN = W.MN_1000
+KERR = W.Camera(M=0.5, S=0.24, Q=0.0, r0=15.0, theta0=80 * W.DEG, fov_deg=30.0, res_x=20,
+                res_y=15)
+
+
+# ----------------------------------------------------------------- FP64 plain
+def test_fp64_schwarzschild_literal_full_image(tracer, oracle):
+    """64x64 Schwarzschild camera, 2000 steps (every ray MAXSTEPS), all 4096 rays."""
+    got = run_gpu(tracer, SCHW, 2000, 1.5e-4)
+    ref = run_oracle(oracle, SCHW, 2000, 1.5e-4)
+    assert_fp64_parity(got, ref, what="schw64")
+    assert np.all(ref["status"] == oracle.MAXSTEPS)
+
+
+def test_fp64_schwarzschild_terminating(tracer, oracle):
+    """24x20 Schwarzschild image with a step cap high enough for every ray to escape or
+    fall in; photon-ring band |b - 3 sqrt(3) M| < 1e-3 M excluded."""
+    cam = W.sub_camera(SCHW, 24, 20)
+    got = run_gpu(tracer, cam, 400000, 1.5e-4)
+    ref = run_oracle(oracle, cam, 400000, 1.5e-4, want_min_sin=True)
+    band = schwarzschild_band(oracle, cam, cam.M) | (ref["min_sin"] < 1e-3)
+    assert_fp64_parity(got, ref, exclude=band, what="schw T")
+    st = ref["status"][~band]
+    assert (st == oracle.HORIZON).sum() > 20 and (st == oracle.ESCAPED).sum() > 100
+
+
+def test_fp64_kerr_terminating(tracer, oracle):
+    """Kerr a = 0.96M at 80 deg inclination, narrow FOV so the shadow spans many pixels."""
+    got = run_gpu(tracer, KERR, 500000, 1.5e-4)
+    ref = run_oracle(oracle, KERR, 500000, 1.5e-4, want_min_sin=True)
+    band = neighbour_band(ref["status"], KERR.res_x, KERR.res_y) | (ref["min_sin"] < 1e-3)
+    assert_fp64_parity(got, ref, exclude=band, what="kerr T")
+    st = ref["status"][~band]
+    assert (st == oracle.HORIZON).sum() > 10 and (st == oracle.ESCAPED).sum() > 10
+
+
+def test_fp64_mn_literal(tracer, oracle):
+    """Manko-Novikov (M=0.5, S=0.24, q=2), r0 = 30M, 80 deg, 20,000 steps, 24x16."""
+    cam = W.sub_camera(MN, 24, 16)
+    got = run_gpu(tracer, cam, 20000, 1.5e-4)
+    ref = run_oracle(oracle, cam, 20000, 1.5e-4)
+    assert_fp64_parity(got, ref, what="mn literal")
+
+
+def test_fp64_mn_terminating(tracer, oracle):
+    """Manko-Novikov with the listing's 500,000-step cap on a 10x8 image."""
+    cam = W.sub_camera(MN, 10, 8)
+    got = run_gpu(tracer, cam, 500000, 1.5e-4)
+    ref = run_oracle(oracle, cam, 500000, 1.5e-4, want_min_sin=True)
+    band = neighbour_band(ref["status"], cam.res_x, cam.res_y) | (ref["min_sin"] < 1e-3)
+    assert_fp64_parity(got, ref, exclude=band, what="mn T")
+
+
+def test_fp64_range_trace_matches_full_image(tracer):
+    """gt_trace_range over a ragged pixel range reproduces the full-image result bitwise."""
+    cam = W.sub_camera(MN, 24, 16)
+    full = run_gpu(tracer, cam, 3000, 1.5e-4)
+    part = to_numpy(tracer.trace_range(37, 201, 3000, 1.5e-4))
+    torch.cuda.synchronize()
+    for k in ("t", "r", "th", "ph", "status", "nsteps"):
+        assert np.array_equal(part[k], full[k][37:238]), k
+
+
+def test_fp64_full_size_sampled(tracer, oracle):
+    """The 1000x1000 Manko-Novikov camera at full size (ray range of 64 image rows, the
+    FP64 benchmark leg's launch) against the oracle on 48 sampled pixels."""
+    tracer.set_spacetime(MN.M, MN.S, MN.Q)
+    tracer.set_camera(MN.r0, MN.theta0, MN.fov_deg, MN.res_x, MN.res_y)
+    tracer.set_options()
+    first, count = 468 * 1000, 64 * 1000
+    got = to_numpy(tracer.trace_range(first, count, 20000, 1.5e-4))
+    torch.cuda.synchronize()
+    pix = first + W.sample_pixels(count, 48, seed=5)
+    ref = run_oracle(oracle, MN, 20000, 1.5e-4, pixels=pix)
+    sub = {k: v[pix - first] for k, v in got.items()}
+    assert_fp64_parity(sub, ref, what="mn full sampled")
+
+
+# ----------------------------------------------------------------- determinism
+@pytest.mark.parametrize("cam,n_steps", [(W.sub_camera(SCHW, 24, 20), 400000),
+                                         (W.sub_camera(MN, 24, 16), 3000)])
+def test_bitwise_independent_of_launch_shape(tracer, cam, n_steps):
+    """Same bits for every block size, grid size and persistent vs one-ray-per-thread."""
+    base = run_gpu(tracer, cam, n_steps, 1.5e-4)
+    for opts in (dict(block_size=32, blocks_per_sm=1), dict(block_size=256, blocks_per_sm=2),
+                 dict(block_size=64, flags=4)):
+        other = run_gpu(tracer, cam, n_steps, 1.5e-4, **opts)
+        for k in ("t", "r", "th", "ph", "status", "nsteps"):
+            assert np.array_equal(other[k], base[k]), (opts, k)
+
+
+# ----------------------------------------------------------------- edge cases
+@pytest.mark.parametrize("rx,ry", [(1, 1), (1, 7), (7, 1), (33, 17)])
+def test_degenerate_and_ragged_images(tracer, oracle, rx, ry):
+    cam = W.sub_camera(MN, rx, ry)
+    got = run_gpu(tracer, cam, 1500, 1.5e-4)
+    ref = run_oracle(oracle, cam, 1500, 1.5e-4)
+    assert_fp64_parity(got, ref, what=f"{rx}x{ry}")
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_zero_steps_returns_camera_state(tracer, mode):
+    cam = W.sub_camera(MN, 5, 3)
+    got = run_gpu(tracer, cam, 0, 1.5e-4, mode)
+    assert np.all(got["status"] == 2) and np.all(got["nsteps"] == 0)
+    assert np.all(got["r"] == cam.r0) and np.all(got["th"] == cam.theta0)
+    assert np.all(got["t"] == 0) and np.all(got["ph"] == 0)
+
+
+def test_compat_flags_match_oracle(tracer, oracle):
+    """The listing's 0.1667 weights and v^phi = alpha camera, both sides."""
+    cam = W.Camera(M=0.5, S=0.24, Q=0.0, r0=15.0, theta0=1.1, fov_deg=75.0, res_x=9, res_y=7)
+    got = run_gpu(tracer, cam, 5000, 1.5e-4, flags=1 | 2)
+    ref = run_oracle(oracle, cam, 5000, 1.5e-4, flags=1 | 2)
+    assert_fp64_parity(got, ref, what="compat")
+
+
+def test_invalid_arguments(g, tracer):
+    lib, ctx = tracer.lib, tracer.ctx
+    assert lib.gt_set_spacetime(ctx, 0.5, 0.25, 0.0) == -1    # |S| >= M^2
+    assert lib.gt_set_spacetime(ctx, 0.5, 0.0, 1.0) == -1     # q != 0 needs S != 0
+    assert lib.gt_set_spacetime(ctx, -1.0, 0.0, 0.0) == -1
+    assert lib.gt_set_camera(ctx, 15.0, 0.0, 75.0, 4, 4) == -1
+    assert lib.gt_set_camera(ctx, 15.0, 1.0, 180.0, 4, 4) == -1
+    assert lib.gt_set_camera(ctx, 15.0, 1.0, 75.0, 0, 4) == -1
+    buf = torch.empty(64, dtype=torch.float64, device="cuda")
+    p = buf.data_ptr()
+    assert lib.gt_trace(ctx, 10, 1.5e-4, 0, p, p, p, p, None, None) == -2  # not configured
+    assert lib.gt_set_spacetime(ctx, 0.5, 0.24, 0.0) == 0
+    assert lib.gt_set_camera(ctx, 15.0, 1.0, 75.0, 4, 4) == 0
+    assert lib.gt_trace(ctx, 10, 0.0, 0, p, p, p, p, None, None) == -1     # sp <= 0
+    assert lib.gt_trace(ctx, -1, 1e-4, 0, p, p, p, p, None, None) == -1    # n_steps < 0
+    assert lib.gt_trace(ctx, 10, 1e-4, 7, p, p, p, p, None, None) == -1    # bad mode
+    assert lib.gt_trace(ctx, 10, 1e-4, 0, p + 4, p, p, p, None, None) == -1  # misaligned
+    assert lib.gt_trace_range(ctx, 10, 7, 10, 1e-4, 0, p, p, p, p, None, None) == -1
+    # camera inside the ergoregion (g_tt >= 0 at r0 = 0.9 on the equator of a = 0.96M)
+    assert lib.gt_set_camera(ctx, 0.9, math.pi / 2, 75.0, 4, 4) == 0
+    assert lib.gt_trace(ctx, 10, 1e-4, 0, p, p, p, p, None, None) == -1
+    assert lib.gt_sync(ctx) == 0
+
+
+def test_watchdog_stops_long_launch_and_context_survives(g, tracer, oracle):
+    """A launch that would run for minutes is stopped by the device watchdog: the call
+    returns GT_ERR_TIMEOUT, every ray carries a status, and the context keeps working."""
+    cam = W.sub_camera(MN, 256, 256)
+    tracer.set_spacetime(cam.M, cam.S, cam.Q)
+    tracer.set_camera(cam.r0, cam.theta0, cam.fov_deg, cam.res_x, cam.res_y)
+    tracer.set_options(timeout_seconds=0.2)
+    with pytest.raises(g.GeotraceError) as e:
+        out = tracer.alloc_outputs(cam.n_rays)
+        out["status"].fill_(99)
+        tracer.trace(500000, 1.5e-4, 0, out=out)
+    assert e.value.code == -5
+    st = out["status"].cpu().numpy()
+    assert np.all(st <= 4) and (st == 4).sum() > 0
+    small = W.sub_camera(MN, 6, 5)
+    got = run_gpu(tracer, small, 800, 1.5e-4)  # options reset to defaults here
+    ref = run_oracle(oracle, small, 800, 1.5e-4)
+    assert_fp64_parity(got, ref, what="after timeout")
+
+
+def test_host_api_matches_device_api(tracer):
+    cam = W.sub_camera(MN, 19, 11)
+    dev = run_gpu(tracer, cam, 2500, 1.5e-4)
+    host = tracer.trace_host(2500, 1.5e-4, 0)
+    for k in ("t", "r", "th", "ph", "status", "nsteps"):
+        assert np.array_equal(np.asarray(host[k]), dev[k]), k
+
+
+def test_batch_matches_single_camera_traces(tracer, oracle):
+    """One persistent launch over uneven cameras equals tracing each camera alone
+    (bitwise for an all-Kerr batch); a mixed Kerr + Manko-Novikov batch matches the oracle."""
+    cams = [W.Camera(0.5, 0.1, 0.0, 12.0, 0.7, 75.0, 13, 9),
+            W.Camera(0.5, 0.2475, 0.0, 20.0, 1.5, 60.0, 5, 17),
+            W.Camera(0.5, 0.0, 0.0, 9.0, 1.2, 75.0, 21, 3)]
+    out = to_numpy(tracer.trace_batch(cams, 3000, 1.5e-4, 0))
+    torch.cuda.synchronize()
+    off = 0
+    for c in cams:
+        single = run_gpu(tracer, c, 3000, 1.5e-4)
+        for k in ("t", "r", "th", "ph", "status", "nsteps"):
+            assert np.array_equal(out[k][off:off + c.n_rays], single[k]), k
+        off += c.n_rays
+    mixed = cams + [W.Camera(0.5, 0.24, 2.0, 15.0, 1.3, 75.0, 7, 6)]
+    out = to_numpy(tracer.trace_batch(mixed, 3000, 1.5e-4, 0))
+    torch.cuda.synchronize()
+    off = 0
+    for c in mixed:
+        ref = run_oracle(oracle, c, 3000, 1.5e-4)
+        sub = {k: v[off:off + c.n_rays] for k, v in out.items()}
+        assert_fp64_parity(sub, ref, what="batch")
+        off += c.n_rays
+
+
+# ----------------------------------------------------------------- FP32-mixed
+def test_mixed_literal_mn(tracer, oracle):
+    cam = W.sub_camera(MN, 24, 16)
+    got = run_gpu(tracer, cam, 20000, 1.5e-4, mode=1)
+    ref = run_oracle(oracle, cam, 20000, 1.5e-4)
+    rep = mixed_report(got, ref)
+    assert rep["agree"] == 1.0 and rep["max_angle"] < 1e-4, rep
+
+
+@pytest.mark.parametrize("cam,n_steps", [(W.sub_camera(SCHW, 24, 20), 400000), (KERR, 500000)])
+def test_mixed_terminating_classification_and_angle(tracer, oracle, cam, n_steps):
+    got = run_gpu(tracer, cam, n_steps, 1.5e-4, mode=1)
+    ref = run_oracle(oracle, cam, n_steps, 1.5e-4, want_min_sin=True)
+    band = neighbour_band(ref["status"], cam.res_x, cam.res_y) | (ref["min_sin"] < 1e-3)
+    rep = mixed_report(got, ref, exclude=band)
+    assert rep["agree"] >= 0.999 and rep["max_angle_escaped"] <= 1e-3, rep
+
+
+def test_mixed_full_size_sampled(tracer, oracle):
+    """The benchmark launch: 1000x1000 Manko-Novikov, 20,000 steps, FP32-mixed, against
+    the oracle on 64 sampled pixels."""
+    got = run_gpu(tracer, MN, 20000, 1.5e-4, mode=1)
+    pix = W.sample_pixels(MN.n_rays, 64, seed=11)
+    ref = run_oracle(oracle, MN, 20000, 1.5e-4, pixels=pix)
+    sub = {k: v[pix] for k, v in got.items()}
+    rep = mixed_report(sub, ref)
+    assert rep["agree"] == 1.0 and rep["max_angle"] < 1e-4, rep
+    for k in ("t", "r"):
+        assert np.max(np.abs(sub[k] - ref[k]) / np.abs(ref[k])) < 1e-4

@@ -1,0 +1,243 @@
+// mlp.cu -- BF16 tensor-core GEMM on tcgen05 (TMEM accumulators) and the small
+// elementwise kernels of the surrogate network's forward and backward passes.
+//
+// gemm:  C[m, n] = sum_k A[m, k] B[n, k]  (+ bias[n]) (then SiLU)
+//   A element (m, k) at A[m * a_sm + k * a_sk], B element (n, k) at B[n * b_sn + k * b_sk]
+//   (bf16; any strides, so transposed operands need no copy), FP32 accumulation in
+//   TMEM.  One CTA of 128 threads owns a 128 x BN output tile; K runs in chunks of
+//   64 through two shared-memory stages: all threads stage a chunk (16-byte vector
+//   loads when K is contiguous), one thread issues four 128 x BN x 16 MMAs and
+//   commits them to the stage's mbarrier, which the stage's next writer waits on.
+//   Split-K over gridDim.z accumulates into C with atomics.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/geotrace.h"
+#include "mlp.cuh"
+#include "tc_gemm.cuh"
+
+namespace gt {
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;
+constexpr uint32_t WAIT_LIMIT = 1u << 24;
+
+template <int BN>
+struct GemmSmem {
+    static constexpr uint32_t A_BYTES = BM * BK * 2;
+    static constexpr uint32_t B_BYTES = BN * BK * 2;
+    static constexpr uint32_t STAGE = A_BYTES + B_BYTES;
+    static constexpr uint32_t TOTAL = 2 * STAGE + 64;
+    static constexpr uint32_t A_LBO = (BM / 8) * 128; // K-direction core-matrix stride
+    static constexpr uint32_t B_LBO = (BN / 8) * 128;
+};
+
+__device__ __forceinline__ void stage_tile(uint8_t *sm, const __nv_bfloat16 *__restrict__ src,
+                                           int rows_total, int k_total, int64_t s_row,
+                                           int64_t s_k, int row0, int k0, int nrows, uint32_t lbo,
+                                           bool vec_ok)
+{
+    const int tid = threadIdx.x;
+    if (vec_ok) {
+        // 8 consecutive k per 16-byte vector
+        const int nvec = nrows * (BK / 8);
+        for (int v = tid; v < nvec; v += blockDim.x) {
+            const int row = v / (BK / 8), kb = v % (BK / 8);
+            const int gr = row0 + row, gk = k0 + kb * 8;
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (gr < rows_total) {
+                if (gk + 8 <= k_total) {
+                    val = *reinterpret_cast<const uint4 *>(src + (int64_t)gr * s_row + gk);
+                } else if (gk < k_total) {
+                    __nv_bfloat16 tmp[8];
+#pragma unroll
+                    for (int e = 0; e < 8; e++)
+                        tmp[e] = (gk + e < k_total) ? src[(int64_t)gr * s_row + gk + e]
+                                                    : __float2bfloat16(0.0f);
+                    val = *reinterpret_cast<const uint4 *>(tmp);
+                }
+            }
+            *reinterpret_cast<uint4 *>(sm + tc::kmajor_offset(row, kb * 8, lbo)) = val;
+        }
+    } else {
+        // generic strides: consecutive threads take consecutive rows (coalesced when the
+        // source is row-contiguous, i.e. a transposed view)
+        const int n = nrows * BK;
+        for (int e = tid; e < n; e += blockDim.x) {
+            const int row = e % nrows, k = e / nrows;
+            const int gr = row0 + row, gk = k0 + k;
+            __nv_bfloat16 val = __float2bfloat16(0.0f);
+            if (gr < rows_total && gk < k_total) val = src[(int64_t)gr * s_row + (int64_t)gk * s_k];
+            *reinterpret_cast<__nv_bfloat16 *>(sm + tc::kmajor_offset(row, k, lbo)) = val;
+        }
+    }
+}
+
+__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
+
+template <int BN>
+__global__ void __launch_bounds__(128) tc_gemm_kernel(GemmArgs g)
+{
+    using L = GemmSmem<BN>;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 2 * L::STAGE);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + 2 * L::STAGE + 16);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    constexpr uint32_t NCOLS = BN < 32 ? 32 : BN;
+
+    // K range of this split
+    const int nk_total = (g.K + BK - 1) / BK;
+    const int per = (nk_total + gridDim.z - 1) / gridDim.z;
+    const int c_begin = blockIdx.z * per;
+    const int c_end = min(nk_total, c_begin + per);
+    const int nk = c_end > c_begin ? c_end - c_begin : 0;
+
+    if (warp == 0) tc::tmem_alloc(tc::smem_u32(tmem_slot), NCOLS);
+    if (tid == 0) {
+        tc::mbar_init(tc::smem_u32(&mbar[0]), 1);
+        tc::mbar_init(tc::smem_u32(&mbar[1]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    bool ok = true;
+    const bool a_vec = (g.a_sk == 1) && (g.a_sm % 8 == 0) && ((uintptr_t)g.A % 16 == 0);
+    const bool b_vec = (g.b_sk == 1) && (g.b_sn % 8 == 0) && ((uintptr_t)g.B % 16 == 0);
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+
+    for (int c = 0; c < nk && ok; ++c) {
+        const int s = c & 1;
+        if (c >= 2) {
+            ok = tc::mbar_wait(tc::smem_u32(&mbar[s]), (uint32_t)(((c - 2) >> 1) & 1), WAIT_LIMIT);
+            if (!ok) break;
+            tc::fence_after_sync();
+        }
+        uint8_t *As = smem + s * L::STAGE;
+        uint8_t *Bs = As + L::A_BYTES;
+        const int k0 = (c_begin + c) * BK;
+        stage_tile(As, g.A, g.M, g.K, g.a_sm, g.a_sk, m0, k0, BM, L::A_LBO, a_vec);
+        stage_tile(Bs, g.B, g.N, g.K, g.b_sn, g.b_sk, n0, k0, BN, L::B_LBO, b_vec);
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t a_base = tc::smem_u32(As), b_base = tc::smem_u32(Bs);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+                const uint64_t ad = tc::smem_desc(a_base + kk * 2 * L::A_LBO, L::A_LBO, 128);
+                const uint64_t bd = tc::smem_desc(b_base + kk * 2 * L::B_LBO, L::B_LBO, 128);
+                tc::mma_bf16(tmem, ad, bd, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+            }
+            tc::mma_commit(tc::smem_u32(&mbar[s]));
+        }
+    }
+    if (ok && nk > 0) {
+        const int last = nk - 1;
+        ok = tc::mbar_wait(tc::smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1), WAIT_LIMIT);
+    }
+    __syncthreads(); // every thread knows the outcome through its own wait
+    tc::fence_after_sync();
+    if (!ok) {
+        if (tid == 0 && g.err) atomicExch(g.err, 1);
+    } else {
+        const int row = m0 + warp * 32 + lane;
+        for (int cc = 0; cc < BN; cc += 32) {
+            float v[32];
+            if (nk > 0) {
+                tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc, v);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 32; i++) v[i] = 0.0f;
+            }
+            if (row < g.M) {
+#pragma unroll
+                for (int i = 0; i < 32; i++) {
+                    const int col = n0 + cc + i;
+                    if (cc + i >= BN || col >= g.N) continue;
+                    float z = v[i];
+                    if (g.bias && blockIdx.z == 0) z += g.bias[col];
+                    if (g.pre) g.pre[(int64_t)row * g.ld_pre + col] = z;
+                    const float y = g.act == 1 ? silu(z) : z;
+                    if (g.C32) {
+                        float *p = g.C32 + (int64_t)row * g.ldc + col;
+                        if (g.atomic)
+                            atomicAdd(p, y);
+                        else
+                            *p = y;
+                    }
+                    if (g.C16) g.C16[(int64_t)row * g.ldc16 + col] = __float2bfloat16(y);
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, NCOLS);
+}
+
+template <int BN>
+cudaError_t launch_bn(const GemmArgs &g, int splits, cudaStream_t s)
+{
+    using L = GemmSmem<BN>;
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, L::TOTAL);
+    if (e != cudaSuccess) return e;
+    dim3 grid((g.M + BM - 1) / BM, (g.N + BN - 1) / BN, splits);
+    tc_gemm_kernel<BN><<<grid, 128, L::TOTAL, s>>>(g);
+    return cudaGetLastError();
+}
+
+} // namespace
+
+cudaError_t launch_gemm(const GemmArgs &g, int bn, int splits, cudaStream_t s)
+{
+    if (splits < 1) splits = 1;
+    switch (bn) {
+    case 16: return launch_bn<16>(g, splits, s);
+    case 32: return launch_bn<32>(g, splits, s);
+    case 64: return launch_bn<64>(g, splits, s);
+    case 128: return launch_bn<128>(g, splits, s);
+    case 256: return launch_bn<256>(g, splits, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+} // namespace gt
+
+extern "C" int gt_gemm_bf16(int device, void *cuda_stream, int M, int N, int K, const void *A,
+                            int64_t a_sm, int64_t a_sk, const void *B, int64_t b_sn, int64_t b_sk,
+                            const float *bias, int act, float *C, int64_t ldc, int accumulate,
+                            int splits, int bn)
+{
+    if (M < 0 || N < 0 || K < 0 || !A || !B || !C || (act != 0 && act != 1)) return GT_ERR_INVALID_ARG;
+    if (bn != 16 && bn != 32 && bn != 64 && bn != 128 && bn != 256) return GT_ERR_INVALID_ARG;
+    if (splits < 1 || splits > 4096 || ldc < N) return GT_ERR_INVALID_ARG;
+    if (M == 0 || N == 0) return GT_OK;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(device) != cudaSuccess) return GT_ERR_CUDA;
+    gt::GemmArgs g = {};
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.A = (const __nv_bfloat16 *)A;
+    g.a_sm = a_sm;
+    g.a_sk = a_sk;
+    g.B = (const __nv_bfloat16 *)B;
+    g.b_sn = b_sn;
+    g.b_sk = b_sk;
+    g.bias = bias;
+    g.act = act;
+    g.C32 = C;
+    g.ldc = ldc;
+    g.atomic = accumulate || splits > 1;
+    cudaError_t e = gt::launch_gemm(g, bn, splits, (cudaStream_t)cuda_stream);
+    if (prev >= 0) cudaSetDevice(prev);
+    return e == cudaSuccess ? GT_OK : GT_ERR_CUDA;
+}

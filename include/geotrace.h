@@ -156,6 +156,20 @@ int gt_device_sm_count(gt_ctx *ctx, int *out);
  * paper's method.  Errors: GT_ERR_INVALID_ARG, GT_ERR_CUDA. */
 int gt_measure_fma_peak(int device, int fp64, int iters, double *flops_per_s);
 
+/* BF16 tensor-core GEMM on `device` / `cuda_stream` (tcgen05, FP32 accumulation in
+ * tensor memory), the building block of the surrogate network's training and
+ * inference: C[m, n] (+)= act(sum_k A[m, k] B[n, k] + bias[n]) for m < M, n < N.
+ * A (m, k) is read at A[m * a_sm + k * a_sk] and B (n, k) at B[n * b_sn + k * b_sk]
+ * (bf16 device arrays, any strides, so transposed views need no copy); bias is an
+ * optional float32[N]; act 0 = identity, 1 = SiLU; C is float32 row-major with
+ * leading dimension ldc >= N.  accumulate != 0 adds into C atomically; splits > 1
+ * splits K over that many CTAs (implies accumulate: C must be zeroed first).
+ * bn (tile width) is one of 16, 32, 64, 128, 256.  Asynchronous on the stream.
+ * Not part of the paper's method.  Errors: GT_ERR_INVALID_ARG, GT_ERR_CUDA. */
+int gt_gemm_bf16(int device, void *cuda_stream, int M, int N, int K, const void *A, int64_t a_sm,
+                 int64_t a_sk, const void *B, int64_t b_sn, int64_t b_sk, const float *bias,
+                 int act, float *C, int64_t ldc, int accumulate, int splits, int bn);
+
 /* Static description of an error code; never NULL. */
 const char *gt_strerror(int code);
 

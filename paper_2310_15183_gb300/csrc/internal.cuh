@@ -34,7 +34,16 @@ enum : int {
     SCR_WORDS = 4
 };
 
+// Per-ray initial data (surrogate training labels): ray k starts at (0, r0, theta0[k], 0)
+// of the spacetime (M, spin[k] M, q[k]) with direction (alpha[k], beta[k]) in the
+// camera's (v^phi sin theta0, v^theta) plane, v^r = -1.
+struct RayParams {
+    const double *alpha, *beta, *spin, *q, *theta0; // device arrays, spin as a/M... see gt_trace_rays
+    double M, r0, r_switch;
+};
+
 struct TraceArgs {
+    const RayParams *rays; // device pointer; when non-null the camera descriptors are unused
     const CamDesc *cams; // device
     int n_cams;
     int64_t n_rays;   // rays in this launch; output index k is ray first + k

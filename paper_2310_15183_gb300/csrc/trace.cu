@@ -40,11 +40,8 @@ __device__ __forceinline__ uint64_t globaltimer_ns()
 // Spacetime constants (Sec. 2.2.2: a = S/M; Sec. 2.2.3: alpha, k, beta), the pixel
 // ranges V = tan(FOV/2)/r0 and H = atan(tan(V) res_x/res_y) of the listing, and the
 // lower metric at the camera (inverse of g^{mu nu}'s (t, phi) block and diagonal).
-__global__ void camera_setup_kernel(CamDesc *cams, int n, int flags, double r_switch)
+__device__ void setup_desc(CamDesc &d, int flags, double r_switch)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n) return;
-    CamDesc d = cams[c];
     SpacetimeC st = {};
     st.M = d.M;
     if (d.Q != 0.0) {
@@ -98,6 +95,14 @@ __global__ void camera_setup_kernel(CamDesc *cams, int n, int flags, double r_sw
                isfinite(d.gl_thth) && d.gl_rr > 0.0 && d.gl_thth > 0.0)
                   ? 1
                   : 0;
+}
+
+__global__ void camera_setup_kernel(CamDesc *cams, int n, int flags, double r_switch)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    CamDesc d = cams[c];
+    setup_desc(d, flags, r_switch);
     cams[c] = d;
 }
 
@@ -119,12 +124,8 @@ struct Ray64 {
 // Initial data of pixel `local` of camera `c` (Sec. 3.3.1, listing's camera block):
 // v = (T, -1, beta_j, alpha_i / sin theta0), T the root (-B + sqrt(B^2 - 4AC))/(2A)
 // of g(v, v) = 0, v /= |T|, p = g v at (0, r0, theta0, 0).
-__device__ __forceinline__ void camera_init(const CamDesc &c, int64_t local, Ray64 &x)
+__device__ __forceinline__ void camera_init_dir(const CamDesc &c, double al, double bt, Ray64 &x)
 {
-    const int i = (int)(local % c.res_x);
-    const int j = (int)(local / c.res_x);
-    const double al = c.res_x > 1 ? c.H * (double)(2 * i - (c.res_x - 1)) / (double)(c.res_x - 1) : 0.0;
-    const double bt = c.res_y > 1 ? c.V * (double)(2 * j - (c.res_y - 1)) / (double)(c.res_y - 1) : 0.0;
     double vr = -1.0, vth = bt, vph = al * c.inv_sin_th0;
     const double A = c.gl_tt;
     const double B = 2.0 * c.gl_tph * vph;
@@ -143,6 +144,15 @@ __device__ __forceinline__ void camera_init(const CamDesc &c, int64_t local, Ray
     x.pr = c.gl_rr * vr;
     x.pth = c.gl_thth * vth;
     x.pph = c.gl_tph * vt + c.gl_phph * vph;
+}
+
+__device__ __forceinline__ void camera_init(const CamDesc &c, int64_t local, Ray64 &x)
+{
+    const int i = (int)(local % c.res_x);
+    const int j = (int)(local / c.res_x);
+    const double al = c.res_x > 1 ? c.H * (double)(2 * i - (c.res_x - 1)) / (double)(c.res_x - 1) : 0.0;
+    const double bt = c.res_y > 1 ? c.V * (double)(2 * j - (c.res_y - 1)) / (double)(c.res_y - 1) : 0.0;
+    camera_init_dir(c, al, bt, x);
 }
 
 template <int KIND>
@@ -366,6 +376,29 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A, int one_shot)
     // Start ray `rid`; returns false (ray already written) when n_steps == 0.
     auto start = [&](int64_t rid) -> bool {
         id = rid;
+        if (A.rays) { // per-ray spacetime and camera (surrogate training data)
+            CamDesc d;
+            d.M = A.rays->M;
+            d.S = A.rays->spin[rid] * A.rays->M;
+            d.Q = A.rays->q[rid];
+            d.r0 = A.rays->r0;
+            d.th0 = A.rays->theta0[rid];
+            d.fov_deg = 90.0;
+            d.res_x = d.res_y = 1;
+            d.offset = 0;
+            setup_desc(d, A.flags, A.rays->r_switch);
+            st = d.st;
+            r_esc = d.r_escape;
+            r_sw = d.r_switch;
+            camera_init_dir(d, A.rays->alpha[rid], A.rays->beta[rid], x);
+            n = 0;
+            if (!d.valid || A.n_steps <= 0) {
+                store_ray(A, rid, x.t, x.r, x.th, x.ph, d.valid ? GT_RAY_MAXSTEPS : GT_RAY_NONFINITE, 0);
+                return false;
+            }
+            if (MODE == 1) mixed_from64(x, m);
+            return true;
+        }
         if (KIND == 2 || A.n_cams > 1) {
             cam = find_camera(cams, A.n_cams, rid);
             st = cams[cam].st;

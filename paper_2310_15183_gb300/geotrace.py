@@ -26,7 +26,7 @@ FLAG_COMPAT_WEIGHTS, FLAG_COMPAT_CAMERA, FLAG_ONE_SHOT = 1, 2, 4
 # every symbol include/geotrace.h declares
 EXPORTS = ("gt_create", "gt_destroy", "gt_set_stream", "gt_set_spacetime", "gt_set_camera",
            "gt_set_options", "gt_trace", "gt_trace_range", "gt_trace_host", "gt_trace_batch", "gt_sync",
-           "gt_device_sm_count", "gt_measure_fma_peak", "gt_strerror")
+           "gt_device_sm_count", "gt_measure_fma_peak", "gt_gemm_bf16", "gt_strerror")
 
 
 class GeotraceError(RuntimeError):
@@ -75,6 +75,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.gt_sync.argtypes = [vp]
     lib.gt_device_sm_count.argtypes = [vp, ctypes.POINTER(i)]
     lib.gt_measure_fma_peak.argtypes = [i, i, i, ctypes.POINTER(d)]
+    lib.gt_gemm_bf16.argtypes = [i, vp, i, i, i, vp, i64, i64, vp, i64, i64, vp, i, vp, i64,
+                                 i, i, i]
     lib.gt_strerror.argtypes = [i]
     lib.gt_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:

@@ -59,12 +59,18 @@ extern "C" {
 
 /* arithmetic modes */
 #define GT_MODE_FP64 0       /* FP64 end to end */
-#define GT_MODE_FP32_MIXED 1 /* FP32 RK4 with compensated state; FP64 zone and H = 0 re-projection */
+#define GT_MODE_FP32_MIXED 1 /* FP32 RK4 with compensated state; FP64 zone and H = 0 re-projection.
+                              * Runs in rounds (FP32 launch, FP64-zone launch, ...) and returns
+                              * once the work has completed. */
 
 /* option flags */
 #define GT_FLAG_COMPAT_WEIGHTS 1 /* RK4 weights 0.1667 as printed in the listing (default 1/6) */
 #define GT_FLAG_COMPAT_CAMERA 2  /* v^phi = alpha_i as in the listing (default alpha_i/sin theta0) */
 #define GT_FLAG_ONE_SHOT 4       /* one ray per thread instead of the persistent ray queue */
+#define GT_FLAG_GRAPH 8          /* issue the trace as one persistent launch replayed from a CUDA
+                                  * graph (captured once per distinct launch, cached in the
+                                  * context); FP32-mixed then keeps its FP64 zone inline, so the
+                                  * call stays asynchronous */
 
 typedef struct gt_ctx gt_ctx;
 
@@ -73,7 +79,7 @@ typedef struct gt_options {
     int block_size;          /* threads per block, multiple of 32 in [32, 256]; 0 = 128 */
     int blocks_per_sm;       /* persistent grid = min(blocks_per_sm, resident limit) * SMs; 0 = 4 */
     int flags;               /* GT_FLAG_* */
-    int reproject_every;     /* FP32-mixed: steps between H = 0 re-projections; 0 = 64 */
+    int reproject_every;     /* FP32-mixed: steps between H = 0 re-projections; 0 = 256 */
     double r_switch;         /* FP32-mixed: FP64 zone r < r_switch; 0 = automatic, < 0 = none */
     double timeout_seconds;  /* device watchdog (wall clock per launch); 0 = none */
 } gt_options;
@@ -142,6 +148,99 @@ int gt_trace_host(gt_ctx *ctx, int64_t n_steps, double step_precision, int mode,
 int gt_trace_batch(gt_ctx *ctx, const gt_camera_desc *cams, int n_cams, int64_t n_steps,
                    double step_precision, int mode, double *t, double *r, double *theta,
                    double *phi, uint8_t *status, uint32_t *nsteps);
+
+/* Trace n rays whose spacetime and camera differ per ray (the surrogate's training
+ * data): ray k starts at (0, r0, theta0[k], 0) of the spacetime (M, S = spin[k] M^2,
+ * Q = q[k]) -- spin[k] is the dimensionless a/M -- with direction v = (v^t, -1,
+ * beta[k], alpha[k]/sin theta0[k]) completed as in the camera (Sec. 3.3.1).  All
+ * per-ray inputs are float64 DEVICE arrays of n elements; outputs as gt_trace over n
+ * rays.  A ray whose camera position is inside the ergoregion gets GT_RAY_NONFINITE.
+ * Errors as gt_trace. */
+int gt_trace_rays(gt_ctx *ctx, int64_t n, const double *alpha, const double *beta,
+                  const double *spin, const double *q, const double *theta0, double M, double r0,
+                  int64_t n_steps, double step_precision, int mode, double *t, double *r,
+                  double *theta, double *phi, uint8_t *status, uint32_t *nsteps);
+
+/* ---------------------------------------------------------------------------------
+ * Surrogate: an MLP (alpha, beta, spin a/M, q, theta0) -> (escape logit, unit end
+ * direction) with layers 16(5 used) -> 256 -> 256 -> 256 -> 256 -> 16(4 used), SiLU,
+ * BF16 weights and activations on tcgen05 tensor cores with FP32 accumulation, FP32
+ * master weights and AdamW.  Trained on rays traced by the integrator; the integrator
+ * is its fallback.  Not part of the paper's method. */
+typedef struct gt_surrogate gt_surrogate;
+
+/* Input ranges the features are normalised over: camera distance r0 and field of view
+ * (pixel directions), spin a/M in [0, spin_max], |q| <= q_max, theta0 range (rad). */
+typedef struct gt_surrogate_norm {
+    double r0, fov_deg, spin_max, q_max, theta0_min, theta0_max;
+} gt_surrogate_norm;
+
+typedef struct gt_train_cfg {
+    int epochs;          /* passes over the training rays */
+    int batch;           /* rows per step, multiple of 128, <= 2^20 */
+    double lr;           /* peak AdamW learning rate (cosine decay to 0) */
+    double weight_decay; /* decoupled weight decay (weights only) */
+    double dir_weight;   /* weight of the squared end-direction error of escaped rays */
+} gt_train_cfg;
+
+/* Number of float32 parameters (weights row-major [out][in], then bias, per layer). */
+int gt_surrogate_num_params(int64_t *out);
+
+/* Create a network on `device` with seeded LeCun-normal weights and zero biases. */
+int gt_surrogate_create(int device, const gt_surrogate_norm *norm, uint64_t seed,
+                        gt_surrogate **out);
+int gt_surrogate_destroy(gt_surrogate *s);
+
+/* Copy the float32 parameters to / from a host array of gt_surrogate_num_params. */
+int gt_surrogate_get_params(gt_surrogate *s, float *host, int64_t n);
+int gt_surrogate_set_params(gt_surrogate *s, const float *host, int64_t n);
+
+/* Network outputs for n samples (device float64 inputs) into `out` (device float32,
+ * n x 4: logit, direction x, y, z).  Runs on the context's stream. */
+int gt_surrogate_eval(gt_ctx *ctx, gt_surrogate *s, int64_t n, const double *alpha,
+                      const double *beta, const double *spin, const double *q,
+                      const double *theta0, float *out);
+
+/* One forward and backward pass over n <= 2^20 samples (one batch) with labels from
+ * traced rays (status, end theta, end phi): loss = mean(BCE(logit, escaped) +
+ * dir_weight * escaped * |d_pred - d_end|^2).  Gradients to a host array of
+ * gt_surrogate_num_params floats; loss to *loss_host.  For checking the gradients. */
+int gt_surrogate_grad(gt_ctx *ctx, gt_surrogate *s, int64_t n, const double *alpha,
+                      const double *beta, const double *spin, const double *q,
+                      const double *theta0, const uint8_t *status, const double *th_end,
+                      const double *ph_end, float dir_weight, float *grads_host,
+                      float *loss_host);
+
+/* Train on n samples (device arrays; inputs and the traced labels) for cfg->epochs
+ * passes of n / cfg->batch full batches.  Mean loss per epoch to loss_per_epoch (host,
+ * cfg->epochs floats) when not NULL.  Synchronous. */
+int gt_surrogate_train(gt_ctx *ctx, gt_surrogate *s, const gt_train_cfg *cfg, int64_t n,
+                       const double *alpha, const double *beta, const double *spin,
+                       const double *q, const double *theta0, const uint8_t *status,
+                       const double *th_end, const double *ph_end, float *loss_per_epoch);
+
+/* Image of the configured camera through the surrogate: pixels with |logit| >= tau that
+ * are not in the photon-ring band (Kerr: |min_r R(r)/(E^2 r^4)| < band from the pixel's
+ * constants of motion; band = 0 disables) take the network's answer -- status ESCAPED
+ * with end theta, phi from the predicted direction, or HORIZON with NaN angles; t and r
+ * are NaN and nsteps 0 for them.  All other pixels are traced by the integrator (mode,
+ * n_steps, step_precision as gt_trace) and written in place.  Outputs as gt_trace
+ * (device, res_x*res_y each, none may be NULL); *n_fallback receives the number of
+ * integrated pixels.  Synchronous. */
+int gt_surrogate_infer(gt_ctx *ctx, gt_surrogate *s, float tau, double band, int64_t n_steps,
+                       double step_precision, int mode, double *t, double *r, double *theta,
+                       double *phi, uint8_t *status, uint32_t *nsteps, int64_t *n_fallback);
+
+/* Autotuner: time gt_trace_range over `trial_rays` central pixels of the configured
+ * camera for `trial_steps` steps with every candidate launch shape (block size in
+ * {64, 128, 192, 256} x resident blocks per SM in {1, 2, 3, 4, 6, 8}, within the
+ * kernel's occupancy limit), keep the fastest in the context's options, and report it.
+ * With cache_path != NULL the result is looked up first and appended after tuning,
+ * keyed by mode, spacetime kind, SM count and device name (plain text lines).
+ * Synchronous.  Errors: GT_ERR_NOT_CONFIGURED, GT_ERR_INVALID_ARG, GT_ERR_CUDA. */
+int gt_autotune(gt_ctx *ctx, int mode, int64_t trial_rays, int64_t trial_steps,
+                double step_precision, const char *cache_path, int *best_block,
+                int *best_blocks_per_sm, double *best_steps_per_s);
 
 /* Wait for all work issued by the context. */
 int gt_sync(gt_ctx *ctx);

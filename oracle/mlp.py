@@ -1,0 +1,126 @@
+"""FP64 CPU reference of the surrogate network -- TEST INFRASTRUCTURE ONLY.
+
+Plain numpy forward and backward pass of the MLP the CUDA library trains:
+features (alpha, beta, a/M, q, theta0) normalised to about [-1, 1], zero padded to 16,
+layers 16 -> 256 -> 256 -> 256 -> 256 -> 16 with SiLU between them, output
+(escape logit, end-direction vector, 12 unused), loss
+    mean( BCE(logit, y) + w * y * |d_pred - d|^2 ),
+where y = 1 for escaped rays and d = (sin th cos ph, sin th sin ph, cos th) of the end
+position.  With `bf16=True` the values are rounded to bfloat16 (round to nearest even) at
+the points where the GPU stores them in bfloat16 (features, hidden activations, weights
+and the gradients fed to the backward products), so that GPU and CPU gradients can be
+compared closely; with `bf16=False` it is the exact FP64 network, whose gradient a
+finite-difference test pins.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+IN = (16, 256, 256, 256, 256)
+OUT = (256, 256, 256, 256, 16)
+
+
+def n_params() -> int:
+    return sum(o * i + o for i, o in zip(IN, OUT))
+
+
+def split(params: np.ndarray):
+    """Weights [out, in] and biases of each layer from the flat parameter vector."""
+    ws, bs, off = [], [], 0
+    for i, o in zip(IN, OUT):
+        ws.append(params[off:off + o * i].reshape(o, i))
+        off += o * i
+        bs.append(params[off:off + o])
+        off += o
+    return ws, bs
+
+
+def bf16(x) -> np.ndarray:
+    """Round to bfloat16 (nearest even) through float32; returned as float64."""
+    f = np.asarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def features(alpha, beta, spin, q, theta0, r0=15.0, fov_deg=75.0, spin_max=0.99, q_max=2.0,
+             th_min=5 * math.pi / 180, th_max=math.pi / 2):
+    V = math.tan(0.5 * fov_deg / 180 * math.pi) / r0
+    H = math.atan(math.tan(V))
+    X = np.zeros((len(alpha), 16))
+    X[:, 0] = np.asarray(alpha) / H
+    X[:, 1] = np.asarray(beta) / V
+    X[:, 2] = np.asarray(spin) * (2 / spin_max) - 1
+    X[:, 3] = np.asarray(q) / q_max
+    X[:, 4] = np.asarray(theta0) * (2 / (th_max - th_min)) - (th_max + th_min) / (th_max - th_min)
+    return X
+
+
+def labels(status, th, ph):
+    y = (np.asarray(status) == 0).astype(np.float64)
+    d = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], axis=1)
+    return y, d * y[:, None]
+
+
+def silu(z):
+    return z / (1 + np.exp(-z))
+
+
+def dsilu(z):
+    s = 1 / (1 + np.exp(-z))
+    return s * (1 + z * (1 - s))
+
+
+def forward(params, X0, bf=True):
+    """Returns the layer inputs X[0..4] and pre-activations Z[0..4]."""
+    r = bf16 if bf else (lambda a: np.asarray(a, dtype=np.float64))
+    ws, bs = split(params)
+    Xs, Zs = [r(X0)], []
+    for l in range(5):
+        Z = Xs[-1] @ r(ws[l]).T + bs[l]
+        Zs.append(Z)
+        if l < 4:
+            Xs.append(r(silu(Z)))
+    return Xs, Zs
+
+
+def loss_and_grad(params, X0, y, d, w_dir, bf=True):
+    r = bf16 if bf else (lambda a: np.asarray(a, dtype=np.float64))
+    ws, _ = split(params)
+    Xs, Zs = forward(params, X0, bf)
+    n = X0.shape[0]
+    z = Zs[4]
+    zl = z[:, 0]
+    bce = np.maximum(zl, 0) - zl * y + np.log1p(np.exp(-np.abs(zl)))
+    diff = z[:, 1:4] - d
+    loss = np.mean(bce + w_dir * y * np.sum(diff * diff, axis=1))
+    dZ = np.zeros_like(z)
+    dZ[:, 0] = (1 / (1 + np.exp(-zl)) - y) / n
+    dZ[:, 1:4] = 2 * w_dir * y[:, None] * diff / n
+    grads = []
+    for l in range(4, -1, -1):
+        dW = r(dZ).T @ Xs[l]
+        db = dZ.sum(axis=0)
+        grads.append((l, dW, db))
+        if l > 0:
+            dX = r(dZ) @ r(ws[l])
+            dZ = dX * dsilu(Zs[l - 1])
+    g = np.zeros_like(params, dtype=np.float64)
+    gw, gb = split(g)
+    for l, dW, db in grads:
+        gw[l][...] = dW
+        gb[l][...] = db
+    return loss, g, z
+
+
+def init_params(seed=0):
+    """Seeded LeCun-normal weights, zero biases (for CPU-only tests)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    p = np.zeros(n_params())
+    ws, _ = split(p)
+    for l, w in enumerate(ws):
+        fan = 5 if l == 0 else IN[l]
+        w[...] = rng.normal(0, 1 / math.sqrt(fan), w.shape)
+    return p

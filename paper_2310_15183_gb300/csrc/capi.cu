@@ -3,6 +3,7 @@
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <new>
@@ -36,7 +37,29 @@ struct gt_ctx {
     // staging for gt_trace_host
     void *d_stage = nullptr;
     size_t stage_bytes = 0;
+    // FP32-mixed park lists (two, capacity park_cap items each)
+    gt::ParkItem *d_park = nullptr;
+    unsigned long long park_cap = 0;
+    // CUDA graph of the last GT_FLAG_GRAPH launch (capture stream, key, executable)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    gt::TraceArgs graph_key = {};
+    int graph_kmode = -1, graph_kind = -1, graph_block = 0, graph_grid = 0;
+    // per-ray parameter block (gt_trace_rays) and surrogate fallback list
+    gt::RayParams *d_rays = nullptr;
+    int64_t *d_fallback = nullptr;
+    int64_t fallback_cap = 0;
 };
+
+cudaStream_t gt_internal_stream(gt_ctx *c) { return c->stream; }
+
+namespace gt {
+namespace sg {
+int infer_chunks(gt_surrogate *s, const CamDesc *d_cam, int64_t n_pix, float tau, double band,
+                 double *t, double *r, double *th, double *ph, uint8_t *status, uint32_t *nsteps,
+                 int64_t *d_fallback, unsigned long long *d_nfb, cudaStream_t st);
+}
+} // namespace gt
 
 namespace {
 
@@ -98,7 +121,7 @@ gt_options effective(const gt_options &o)
     gt_options e = o;
     if (e.block_size == 0) e.block_size = 128;
     if (e.blocks_per_sm == 0) e.blocks_per_sm = 4;
-    if (e.reproject_every == 0) e.reproject_every = 64;
+    if (e.reproject_every == 0) e.reproject_every = 256;
     return e;
 }
 
@@ -122,9 +145,97 @@ int prepare_camera(gt_ctx *c)
     return GT_OK;
 }
 
+int grid_for(gt_ctx *c, const gt_options &e, int kmode, int kind_hint, int64_t n_work, bool one_shot,
+             int *grid)
+{
+    if (one_shot) {
+        const int64_t g = (n_work + e.block_size - 1) / e.block_size;
+        if (g > 0x7fffffff) return GT_ERR_INVALID_ARG;
+        *grid = g > 0 ? (int)g : 1;
+    } else {
+        // persistent grid: never more blocks than can be resident at once
+        const int fit = gt::max_blocks_per_sm(kmode, kind_hint, e.block_size);
+        *grid = (e.blocks_per_sm < fit ? e.blocks_per_sm : fit) * c->sm_count;
+    }
+    return GT_OK;
+}
+
+// FP32-mixed runs in rounds on the context's stream: an FP32 launch over the fresh rays
+// parks every ray that enters the FP64 zone; an FP64 launch integrates the parked rays
+// until they leave the zone (parked again) or stop; an FP32 launch continues the
+// returned rays; and so on until no ray is parked.  The host reads the park count
+// between rounds, so this mode returns after the work has completed.
+int run_mixed_rounds(gt_ctx *c, gt::TraceArgs &a, int kind_hint, const gt_options &e, bool one_shot)
+{
+    const unsigned long long need = (unsigned long long)a.n_rays;
+    if (c->park_cap < need) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->d_park);
+        c->d_park = nullptr;
+        c->park_cap = 0;
+        cudaError_t err = cudaMalloc(&c->d_park, 2 * need * sizeof(gt::ParkItem));
+        if (err != cudaSuccess) return cuda_code(err);
+        c->park_cap = need;
+    }
+    gt::ParkItem *listA = c->d_park, *listB = c->d_park + c->park_cap;
+    unsigned long long *w = c->d_scratch;
+    a.out_cap = c->park_cap;
+    a.in_cap = c->park_cap;
+    int grid;
+    // round 0: FP32 over the fresh rays, zone entries parked on A
+    a.in_items = listB;
+    a.in_count = w + gt::SCR_TO32; // zero
+    a.out_items = listA;
+    a.out_count = w + gt::SCR_TO64;
+    int rc = grid_for(c, e, gt::KMODE_MIXED_FP32, kind_hint, a.n_fresh, one_shot, &grid);
+    if (rc != GT_OK) return rc;
+    cudaError_t err = gt::launch_trace(a, gt::KMODE_MIXED_FP32, kind_hint, e.block_size, grid,
+                                       one_shot, c->stream);
+    if (err != cudaSuccess) return cuda_code(err);
+    for (int round = 0; round < 100000; ++round) {
+        unsigned long long parked = 0;
+        err = cudaMemcpyAsync(&parked, w + gt::SCR_TO64, sizeof parked, cudaMemcpyDeviceToHost,
+                              c->stream);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(c->stream);
+        if (err != cudaSuccess) return cuda_code(err);
+        if (parked == 0) return GT_OK;
+        // FP64 zone: A -> (B, finished)
+        a.n_fresh = 0;
+        a.in_items = listA;
+        a.in_count = w + gt::SCR_TO64;
+        a.out_items = listB;
+        a.out_count = w + gt::SCR_TO32;
+        err = cudaMemsetAsync(w + gt::SCR_NEXT_RAY, 0, sizeof(unsigned long long), c->stream);
+        if (err == cudaSuccess)
+            err = cudaMemsetAsync(w + gt::SCR_TO32, 0, sizeof(unsigned long long), c->stream);
+        if (err != cudaSuccess) return cuda_code(err);
+        rc = grid_for(c, e, gt::KMODE_ZONE_FP64, kind_hint, (int64_t)parked, one_shot, &grid);
+        if (rc != GT_OK) return rc;
+        err = gt::launch_trace(a, gt::KMODE_ZONE_FP64, kind_hint, e.block_size, grid, one_shot,
+                               c->stream);
+        if (err != cudaSuccess) return cuda_code(err);
+        // FP32 continuation: B -> (A, finished)
+        a.in_items = listB;
+        a.in_count = w + gt::SCR_TO32;
+        a.out_items = listA;
+        a.out_count = w + gt::SCR_TO64;
+        err = cudaMemsetAsync(w + gt::SCR_NEXT_RAY, 0, sizeof(unsigned long long), c->stream);
+        if (err == cudaSuccess)
+            err = cudaMemsetAsync(w + gt::SCR_TO64, 0, sizeof(unsigned long long), c->stream);
+        if (err != cudaSuccess) return cuda_code(err);
+        rc = grid_for(c, e, gt::KMODE_MIXED_FP32, kind_hint, (int64_t)parked, one_shot, &grid);
+        if (rc != GT_OK) return rc;
+        err = gt::launch_trace(a, gt::KMODE_MIXED_FP32, kind_hint, e.block_size, grid, one_shot,
+                               c->stream);
+        if (err != cudaSuccess) return cuda_code(err);
+    }
+    return GT_ERR_CUDA;
+}
+
 int run_trace(gt_ctx *c, const CamDesc *d_cams, int n_cams, int kind_hint, int64_t first,
-              int64_t n_rays, int64_t n_steps, double sp, int mode, double *t, double *r, double *th, double *ph,
-              uint8_t *status, uint32_t *nsteps)
+              int64_t n_rays, int64_t n_steps, double sp, int mode, double *t, double *r,
+              double *th, double *ph, uint8_t *status, uint32_t *nsteps,
+              const int64_t *fresh_ids = nullptr, const gt::RayParams *d_rays = nullptr)
 {
     const gt_options e = effective(c->opts);
     if (n_rays == 0) return GT_OK;
@@ -133,7 +244,10 @@ int run_trace(gt_ctx *c, const CamDesc *d_cams, int n_cams, int kind_hint, int64
     a.cams = d_cams;
     a.n_cams = n_cams;
     a.n_rays = n_rays;
+    a.n_fresh = n_rays;
     a.first = first;
+    a.fresh_ids = fresh_ids;
+    a.rays = d_rays;
     a.n_steps = n_steps;
     a.sp = sp;
     a.w6 = (e.flags & GT_FLAG_COMPAT_WEIGHTS) ? 0.1667 : 1.0 / 6.0;
@@ -151,18 +265,62 @@ int run_trace(gt_ctx *c, const CamDesc *d_cams, int n_cams, int kind_hint, int64
         cudaMemsetAsync(c->d_scratch, 0, gt::SCR_WORDS * sizeof(unsigned long long), c->stream);
     if (err != cudaSuccess) return cuda_code(err);
     const bool one_shot = (e.flags & GT_FLAG_ONE_SHOT) != 0;
-    int grid;
-    if (one_shot) {
-        const int64_t g = (n_rays + e.block_size - 1) / e.block_size;
-        if (g > 0x7fffffff) return GT_ERR_INVALID_ARG;
-        grid = (int)g;
+    int rc;
+    if (e.flags & GT_FLAG_GRAPH) {
+        // one persistent launch (FP32-mixed with its FP64 zone inline) replayed from a
+        // CUDA graph; the graph is captured once per distinct launch and cached
+        const int kmode = mode == GT_MODE_FP64 ? gt::KMODE_FP64 : gt::KMODE_MIXED_INLINE;
+        int grid;
+        rc = grid_for(c, e, kmode, kind_hint, n_rays, one_shot, &grid);
+        if (rc != GT_OK) return rc;
+        const bool same = c->graph_exec && memcmp(&c->graph_key, &a, sizeof a) == 0 &&
+                          c->graph_kmode == kmode && c->graph_kind == kind_hint &&
+                          c->graph_block == e.block_size && c->graph_grid == grid;
+        if (!same) {
+            if (!c->cap_stream) {
+                err = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+                if (err != cudaSuccess) return cuda_code(err);
+            }
+            if (c->graph_exec) {
+                cudaGraphExecDestroy(c->graph_exec);
+                c->graph_exec = nullptr;
+            }
+            cudaGraph_t graph = nullptr;
+            err = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+            if (err != cudaSuccess) return cuda_code(err);
+            cudaError_t e1 = cudaMemsetAsync(c->d_scratch, 0,
+                                             gt::SCR_WORDS * sizeof(unsigned long long), c->cap_stream);
+            cudaError_t e2 = gt::launch_trace(a, kmode, kind_hint, e.block_size, grid, one_shot,
+                                              c->cap_stream);
+            err = cudaStreamEndCapture(c->cap_stream, &graph);
+            if (e1 != cudaSuccess || e2 != cudaSuccess || err != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                return GT_ERR_CUDA;
+            }
+            err = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (err != cudaSuccess) {
+                c->graph_exec = nullptr;
+                return cuda_code(err);
+            }
+            c->graph_key = a;
+            c->graph_kmode = kmode;
+            c->graph_kind = kind_hint;
+            c->graph_block = e.block_size;
+            c->graph_grid = grid;
+        }
+        rc = cuda_code(cudaGraphLaunch(c->graph_exec, c->stream));
+    } else if (mode == GT_MODE_FP64) {
+        int grid;
+        rc = grid_for(c, e, gt::KMODE_FP64, kind_hint, n_rays, one_shot, &grid);
+        if (rc != GT_OK) return rc;
+        err = gt::launch_trace(a, gt::KMODE_FP64, kind_hint, e.block_size, grid, one_shot,
+                               c->stream);
+        rc = cuda_code(err);
     } else {
-        // persistent grid: never more blocks than can be resident at once
-        const int fit = gt::max_blocks_per_sm(mode, kind_hint, e.block_size);
-        grid = (e.blocks_per_sm < fit ? e.blocks_per_sm : fit) * c->sm_count;
+        rc = run_mixed_rounds(c, a, kind_hint, e, one_shot);
     }
-    err = gt::launch_trace(a, mode, kind_hint, e.block_size, grid, one_shot, c->stream);
-    if (err != cudaSuccess) return cuda_code(err);
+    if (rc != GT_OK) return rc;
     if (a.timeout_ns) {
         unsigned long long flag = 0;
         err = cudaMemcpyAsync(&flag, c->d_scratch + gt::SCR_TIMEOUT, sizeof flag,
@@ -243,6 +401,11 @@ int gt_destroy(gt_ctx *c)
     cudaFree(c->d_batch);
     cudaFree(c->d_scratch);
     cudaFree(c->d_stage);
+    cudaFree(c->d_park);
+    cudaFree(c->d_rays);
+    cudaFree(c->d_fallback);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
     return GT_OK;
 }
@@ -289,7 +452,8 @@ int gt_set_options(gt_ctx *c, const gt_options *o)
     if (v.reproject_every < 0) return GT_ERR_INVALID_ARG;
     if (!isfinite(v.r_switch) || !(v.timeout_seconds >= 0.0) || !isfinite(v.timeout_seconds))
         return GT_ERR_INVALID_ARG;
-    if (v.flags & ~(GT_FLAG_COMPAT_WEIGHTS | GT_FLAG_COMPAT_CAMERA | GT_FLAG_ONE_SHOT))
+    if (v.flags & ~(GT_FLAG_COMPAT_WEIGHTS | GT_FLAG_COMPAT_CAMERA | GT_FLAG_ONE_SHOT |
+                    GT_FLAG_GRAPH))
         return GT_ERR_INVALID_ARG;
     c->opts = v;
     return GT_OK;
@@ -416,6 +580,193 @@ int gt_trace_batch(gt_ctx *c, const gt_camera_desc *cams, int n_cams, int64_t n_
     const int kind = any_mn && any_kerr ? 2 : (any_mn ? gt::KIND_MN : gt::KIND_KERR);
     return run_trace(c, c->d_batch, n_cams, kind, 0, off, n_steps, sp, mode, t, r, th, ph, status,
                      nsteps);
+}
+
+int gt_trace_rays(gt_ctx *c, int64_t n, const double *alpha, const double *beta,
+                  const double *spin, const double *q, const double *theta0, double M, double r0,
+                  int64_t n_steps, double sp, int mode, double *t, double *r, double *th,
+                  double *ph, uint8_t *status, uint32_t *nsteps)
+{
+    int rc = check_common(c, n_steps, sp, mode);
+    if (rc != GT_OK) return rc;
+    if (n < 0 || !alpha || !beta || !spin || !q || !theta0) return GT_ERR_INVALID_ARG;
+    if (!(M > 0.0) || !(r0 > 0.0) || !isfinite(M) || !isfinite(r0)) return GT_ERR_INVALID_ARG;
+    if (!aligned8(t) || !aligned8(r) || !aligned8(th) || !aligned8(ph) || ((uintptr_t)nsteps & 3u))
+        return GT_ERR_INVALID_ARG;
+    if (n == 0) return GT_OK;
+    DeviceGuard g(c->device);
+    if (!g.ok) return GT_ERR_CUDA;
+    if (!c->d_rays) {
+        cudaError_t e = cudaMalloc(&c->d_rays, sizeof(gt::RayParams));
+        if (e != cudaSuccess) return cuda_code(e);
+    }
+    const gt_options e = effective(c->opts);
+    gt::RayParams h;
+    h.alpha = alpha;
+    h.beta = beta;
+    h.spin = spin;
+    h.q = q;
+    h.theta0 = theta0;
+    h.M = M;
+    h.r0 = r0;
+    h.r_switch = e.r_switch;
+    cudaError_t err = cudaMemcpyAsync(c->d_rays, &h, sizeof h, cudaMemcpyHostToDevice, c->stream);
+    if (err != cudaSuccess) return cuda_code(err);
+    // the kernel reads descriptor 0 before the per-ray set-up replaces it
+    return run_trace(c, c->d_cam, 1, 2, 0, n, n_steps, sp, mode, t, r, th, ph, status, nsteps,
+                     nullptr, c->d_rays);
+}
+
+int gt_surrogate_infer(gt_ctx *c, gt_surrogate *s, float tau, double band, int64_t n_steps,
+                       double sp, int mode, double *t, double *r, double *th, double *ph,
+                       uint8_t *status, uint32_t *nsteps, int64_t *n_fallback)
+{
+    int rc = check_common(c, n_steps, sp, mode);
+    if (rc != GT_OK) return rc;
+    if (!s || !t || !r || !th || !ph || !status || !nsteps || !(tau >= 0.0f) || !(band >= 0.0))
+        return GT_ERR_INVALID_ARG;
+    if (!c->st_set || !c->cam_set) return GT_ERR_NOT_CONFIGURED;
+    if (!aligned8(t) || !aligned8(r) || !aligned8(th) || !aligned8(ph) || ((uintptr_t)nsteps & 3u))
+        return GT_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    if (!g.ok) return GT_ERR_CUDA;
+    rc = prepare_camera(c);
+    if (rc != GT_OK) return rc;
+    if (!c->cam_valid) return GT_ERR_INVALID_ARG;
+    const int64_t n_pix = (int64_t)c->res_x * c->res_y;
+    if (c->fallback_cap < n_pix) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->d_fallback);
+        c->d_fallback = nullptr;
+        c->fallback_cap = 0;
+        cudaError_t e = cudaMalloc(&c->d_fallback, n_pix * sizeof(int64_t));
+        if (e != cudaSuccess) return cuda_code(e);
+        c->fallback_cap = n_pix;
+    }
+    unsigned long long *d_nfb = c->d_scratch + gt::SCR_TO32; // free until the fallback trace
+    cudaError_t err = cudaMemsetAsync(d_nfb, 0, sizeof(unsigned long long), c->stream);
+    if (err != cudaSuccess) return cuda_code(err);
+    rc = gt::sg::infer_chunks(s, c->d_cam, n_pix, tau, band, t, r, th, ph, status, nsteps,
+                              c->d_fallback, d_nfb, c->stream);
+    if (rc != GT_OK) return rc;
+    unsigned long long nfb = 0;
+    err = cudaMemcpyAsync(&nfb, d_nfb, sizeof nfb, cudaMemcpyDeviceToHost, c->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(c->stream);
+    if (err != cudaSuccess) return cuda_code(err);
+    if (n_fallback) *n_fallback = (int64_t)nfb;
+    if (nfb == 0) return GT_OK;
+    const int kind = (c->Q != 0.0) ? gt::KIND_MN : gt::KIND_KERR;
+    return run_trace(c, c->d_cam, 1, kind, 0, (int64_t)nfb, n_steps, sp, mode, t, r, th, ph,
+                     status, nsteps, c->d_fallback, nullptr);
+}
+
+int gt_autotune(gt_ctx *c, int mode, int64_t trial_rays, int64_t trial_steps, double sp,
+                const char *cache_path, int *best_block, int *best_blocks_per_sm,
+                double *best_steps_per_s)
+{
+    if (!c || trial_rays < 1 || trial_steps < 1 || !(sp > 0.0)) return GT_ERR_INVALID_ARG;
+    if (mode != GT_MODE_FP64 && mode != GT_MODE_FP32_MIXED) return GT_ERR_INVALID_ARG;
+    if (!c->st_set || !c->cam_set) return GT_ERR_NOT_CONFIGURED;
+    DeviceGuard g(c->device);
+    if (!g.ok) return GT_ERR_CUDA;
+    const int kind = (c->Q != 0.0) ? gt::KIND_MN : gt::KIND_KERR;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess) return GT_ERR_CUDA;
+    char key[256];
+    snprintf(key, sizeof key, "mode=%d kind=%d sms=%d dev=%s", mode, kind, c->sm_count, prop.name);
+    // cached result?
+    if (cache_path) {
+        FILE *f = fopen(cache_path, "r");
+        if (f) {
+            char line[512];
+            while (fgets(line, sizeof line, f)) {
+                int b = 0, k = 0;
+                double v = 0;
+                char *bar = strchr(line, '|');
+                if (!bar) continue;
+                *bar = 0;
+                if (strcmp(line, key) == 0 && sscanf(bar + 1, "%d %d %lf", &b, &k, &v) == 3 &&
+                    b >= 32 && b <= 256 && b % 32 == 0 && k >= 1 && k <= 64) {
+                    fclose(f);
+                    c->opts.block_size = b;
+                    c->opts.blocks_per_sm = k;
+                    if (best_block) *best_block = b;
+                    if (best_blocks_per_sm) *best_blocks_per_sm = k;
+                    if (best_steps_per_s) *best_steps_per_s = v;
+                    return GT_OK;
+                }
+            }
+            fclose(f);
+        }
+    }
+    const int64_t n_pix = (int64_t)c->res_x * c->res_y;
+    const int64_t count = trial_rays < n_pix ? trial_rays : n_pix;
+    const int64_t first = (n_pix - count) / 2;
+    double *buf = nullptr;
+    uint32_t *ns = nullptr;
+    cudaError_t err = cudaMalloc(&buf, count * 4 * sizeof(double));
+    if (err == cudaSuccess) err = cudaMalloc(&ns, count * sizeof(uint32_t));
+    if (err != cudaSuccess) {
+        cudaFree(buf);
+        return cuda_code(err);
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const gt_options saved = c->opts;
+    const int blocks[] = {64, 128, 192, 256};
+    const int per_sm[] = {1, 2, 3, 4, 6, 8};
+    int bb = 128, bk = 4;
+    double bv = -1.0;
+    int rc = GT_OK;
+    for (int bi = 0; bi < 4 && rc == GT_OK; bi++) {
+        const int kmode = mode == GT_MODE_FP64 ? gt::KMODE_FP64 : gt::KMODE_MIXED_FP32;
+        const int fit = gt::max_blocks_per_sm(kmode, kind, blocks[bi]);
+        for (int ki = 0; ki < 6 && rc == GT_OK; ki++) {
+            if (per_sm[ki] > fit) continue;
+            c->opts = saved;
+            c->opts.block_size = blocks[bi];
+            c->opts.blocks_per_sm = per_sm[ki];
+            c->opts.timeout_seconds = 0.0;
+            double best_ms = 1e300;
+            for (int rep = 0; rep < 2 && rc == GT_OK; rep++) {
+                cudaEventRecord(e0, c->stream);
+                rc = gt_trace_range(c, first, count, trial_steps, sp, mode, buf, buf + count,
+                                    buf + 2 * count, buf + 3 * count, nullptr, ns);
+                cudaEventRecord(e1, c->stream);
+                if (cudaEventSynchronize(e1) != cudaSuccess) rc = GT_ERR_CUDA;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0 && ms < best_ms) best_ms = ms; // first run warms up
+            }
+            if (rc != GT_OK) break;
+            const double v = (double)count * (double)trial_steps / (best_ms * 1e-3);
+            if (v > bv) {
+                bv = v;
+                bb = blocks[bi];
+                bk = per_sm[ki];
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(buf);
+    cudaFree(ns);
+    c->opts = saved;
+    if (rc != GT_OK) return rc;
+    c->opts.block_size = bb;
+    c->opts.blocks_per_sm = bk;
+    if (best_block) *best_block = bb;
+    if (best_blocks_per_sm) *best_blocks_per_sm = bk;
+    if (best_steps_per_s) *best_steps_per_s = bv;
+    if (cache_path) {
+        FILE *f = fopen(cache_path, "a");
+        if (f) {
+            fprintf(f, "%s|%d %d %.6g\n", key, bb, bk, bv);
+            fclose(f);
+        }
+    }
+    return GT_OK;
 }
 
 int gt_sync(gt_ctx *c)

@@ -4,7 +4,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/geotrace.h"
 #include "spacetime.cuh"
+
+// The context's stream (capi.cu).
+cudaStream_t gt_internal_stream(gt_ctx *c);
 
 namespace gt {
 
@@ -29,9 +33,22 @@ struct CamDesc {
 
 // Scratch words of one launch (device memory owned by the context).
 enum : int {
-    SCR_NEXT_RAY = 0,   // persistent queue: next unclaimed ray id
+    SCR_NEXT_RAY = 0,   // persistent queue: next unclaimed work item
     SCR_TIMEOUT = 1,    // set to 1 by the watchdog
+    SCR_TO64 = 2,       // FP32-mixed: rays parked for the FP64 zone kernel
+    SCR_TO32 = 3,       // FP32-mixed: rays handed back to the FP32 kernel
     SCR_WORDS = 4
+};
+
+// Kernel modes (public GT_MODE_FP32_MIXED runs MIXED_FP32 and ZONE_FP64 in rounds).
+enum : int { KMODE_FP64 = 0, KMODE_MIXED_INLINE = 1, KMODE_MIXED_FP32 = 2, KMODE_ZONE_FP64 = 3 };
+
+// A ray handed between the FP32 and FP64-zone kernels (full state in FP64).
+struct ParkItem {
+    int64_t id;
+    uint32_t n;
+    int32_t cam;
+    double t, r, th, ph, pr, pth, pt, pph;
 };
 
 // Per-ray initial data (surrogate training labels): ray k starts at (0, r0, theta0[k], 0)
@@ -46,8 +63,18 @@ struct TraceArgs {
     const RayParams *rays; // device pointer; when non-null the camera descriptors are unused
     const CamDesc *cams; // device
     int n_cams;
-    int64_t n_rays;   // rays in this launch; output index k is ray first + k
+    int64_t n_rays;   // rays of the whole trace
+    int64_t n_fresh;  // fresh rays started by this launch, ids [0, n_fresh); output index
+                      // k belongs to flat ray first + k
     int64_t first;    // first flat ray id (single-camera range traces)
+    const int64_t *fresh_ids; // when set, fresh work item w is ray fresh_ids[w] (and its
+                              // output index); otherwise ray w
+    const ParkItem *in_items;                // input list (modes 2, 3) or null
+    const unsigned long long *in_count;      // its length (device word) or null
+    unsigned long long in_cap;               // capacity of the input list
+    ParkItem *out_items;                     // output list (modes 2, 3)
+    unsigned long long *out_count;           // its length (device word)
+    unsigned long long out_cap;
     int64_t n_steps;
     double sp;        // step_precision
     double w6;        // RK4 weight (1/6, or 0.1667 in compat mode)
@@ -64,8 +91,8 @@ struct TraceArgs {
 cudaError_t launch_camera_setup(CamDesc *d_cams, int n_cams, int flags, double r_switch,
                                 cudaStream_t s);
 // Resident blocks per SM of the trace kernel for this block size (>= 1).
-int max_blocks_per_sm(int mode, int kind_hint, int block);
-cudaError_t launch_trace(const TraceArgs &a, int mode, int kind_hint, int block, int grid,
+int max_blocks_per_sm(int kmode, int kind_hint, int block);
+cudaError_t launch_trace(const TraceArgs &a, int kmode, int kind_hint, int block, int grid,
                          bool one_shot, cudaStream_t s);
 
 } // namespace gt

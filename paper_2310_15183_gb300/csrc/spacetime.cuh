@@ -122,6 +122,47 @@ GT_HD D3<T> dexp(D3<T> a)
     return {e, a.r * e, a.t * e};
 }
 
+// Value-only stand-in with the dual numbers' interface: the same formulas evaluate
+// the metric functions without their derivatives (camera set-up, H re-projection).
+template <class T>
+struct V1 {
+    T v;
+};
+template <class T>
+GT_HD V1<T> operator+(V1<T> a, V1<T> b) { return {a.v + b.v}; }
+template <class T>
+GT_HD V1<T> operator-(V1<T> a, V1<T> b) { return {a.v - b.v}; }
+template <class T>
+GT_HD V1<T> operator-(V1<T> a) { return {-a.v}; }
+template <class T>
+GT_HD V1<T> operator+(V1<T> a, T c) { return {a.v + c}; }
+template <class T>
+GT_HD V1<T> operator+(T c, V1<T> a) { return {a.v + c}; }
+template <class T>
+GT_HD V1<T> operator-(V1<T> a, T c) { return {a.v - c}; }
+template <class T>
+GT_HD V1<T> operator-(T c, V1<T> a) { return {c - a.v}; }
+template <class T>
+GT_HD V1<T> operator*(V1<T> a, T c) { return {a.v * c}; }
+template <class T>
+GT_HD V1<T> operator*(T c, V1<T> a) { return {a.v * c}; }
+template <class T>
+GT_HD V1<T> operator*(V1<T> a, V1<T> b) { return {a.v * b.v}; }
+template <class T>
+GT_HD V1<T> dsq(V1<T> a) { return {a.v * a.v}; }
+template <class T>
+GT_HD V1<T> drcp(V1<T> a) { return {T(1) / a.v}; }
+template <class T>
+GT_HD V1<T> drsqrt(V1<T> a) { return {rsqrt_t(a.v)}; }
+template <class T>
+GT_HD V1<T> dexp(V1<T> a) { return {exp_t(a.v)}; }
+
+// variable constructors: f(r) with d/dr = dr, and f(theta) with d/dtheta = dt
+template <class T>
+GT_HD void mkvar(D3<T> &o, T v, T dr, T dt) { o = {v, dr, dt}; }
+template <class T>
+GT_HD void mkvar(V1<T> &o, T v, T, T) { o = {v}; }
+
 // ------------------------------------------------------------------ Kerr
 template <class T>
 GT_HD void kerr_rates(const SpacetimeC &c, T r, T th, T pr, T pth, T pt,
@@ -174,51 +215,53 @@ __device__ __forceinline__ void kerr_upper(const SpacetimeC &c, double r, double
 #endif
 
 // ------------------------------------------------------------------ Manko-Novikov
-template <class T>
+template <class N>
 struct MNPot {
-    D3<T> invf, F, om, G, Delta;
+    N invf, F, om, G, Delta;
 };
 
-template <class T>
-GT_HD void mn_potentials(const SpacetimeC &c, T r, T th, MNPot<T> &P)
+// N = D3<T> (values and r, theta derivatives) or V1<T> (values only).
+template <class T, class N>
+GT_HD void mn_potentials(const SpacetimeC &c, T r, T th, MNPot<N> &P)
 {
     T s, cs;
     sincos_t(th, &s, &cs);
     const T ik = T(c.ik);
     const T two_beta = T(c.two_beta);
-    const D3<T> x = {(r - T(c.M)) * ik, ik, T(0)};
-    const D3<T> xm1 = {(r - T(c.r_plus)) * ik, ik, T(0)}; // x - 1 without cancellation
-    const D3<T> xp1 = x + T(1);
-    const D3<T> y = {cs, T(0), -s};
-    const D3<T> s2 = {s * s, T(0), T(2) * s * cs}; // 1 - y^2
-    const D3<T> x2m1 = xm1 * xp1;
-    const D3<T> R2 = x2m1 + dsq(y); // x^2 + y^2 - 1
-    const D3<T> iR = drsqrt(R2);
-    const D3<T> u = x * y * iR; // Legendre argument x y / R
-    const D3<T> u2 = dsq(u);
-    const D3<T> P2 = u2 * T(1.5) - T(0.5);
-    const D3<T> P3 = u * (u2 * T(2.5) - T(1.5));
-    const D3<T> iR2 = dsq(iR);
-    const D3<T> iR3 = iR2 * iR;
-    const D3<T> uR2 = u * iR2, P2R3 = P2 * iR3;
+    N x, xm1, y, s2;
+    mkvar(x, (r - T(c.M)) * ik, ik, T(0));
+    mkvar(xm1, (r - T(c.r_plus)) * ik, ik, T(0)); // x - 1 without cancellation
+    mkvar(y, cs, T(0), -s);
+    mkvar(s2, s * s, T(0), T(2) * s * cs); // 1 - y^2
+    const N xp1 = x + T(1);
+    const N x2m1 = xm1 * xp1;
+    const N R2 = x2m1 + dsq(y); // x^2 + y^2 - 1
+    const N iR = drsqrt(R2);
+    const N u = x * y * iR; // Legendre argument x y / R
+    const N u2 = dsq(u);
+    const N P2 = u2 * T(1.5) - T(0.5);
+    const N P3 = u * (u2 * T(2.5) - T(1.5));
+    const N iR2 = dsq(iR);
+    const N iR3 = iR2 * iR;
+    const N uR2 = u * iR2, P2R3 = P2 * iR3;
     // sum_l (+-1) P_l / R^{l+1} with the sign patterns of fraktur a, fraktur b, gamma'
-    const D3<T> Sa = (x - y) * (iR + uR2 + P2R3);
-    const D3<T> Sb = (x + y) * (uR2 - iR - P2R3);
-    const D3<T> Sg = T(2) * (x * iR - y * uR2 + x * P2R3);
-    const D3<T> fa = dexp((Sa - T(1)) * (-two_beta)) * T(-c.alpha);
-    const D3<T> fb = dexp((Sb + T(1)) * two_beta) * T(c.alpha);
-    const D3<T> ab = fa * fb;
-    const D3<T> opab = ab + T(1);
-    const D3<T> bma = fb - fa;
-    const D3<T> A = x2m1 * dsq(opab) - s2 * dsq(bma);
-    const D3<T> B = dsq(xp1 + xm1 * ab) + dsq((y + T(1)) * fa + (T(1) - y) * fb);
-    const D3<T> C = x2m1 * opab * (bma - y * (fa + fb)) + s2 * bma * (opab + x * (T(1) - ab));
-    const D3<T> psi2 = P2R3 * two_beta;                                   // 2 psi
-    const D3<T> g2 = T(c.three_beta2) * dsq(iR3) * (dsq(P3) - dsq(P2)) + (Sg - T(2)) * two_beta; // 2 gamma''
-    const D3<T> e2psi = dexp(psi2);
-    const D3<T> ie2psi = drcp(e2psi);
-    const D3<T> iA = drcp(A);
-    const D3<T> iB = drcp(B);
+    const N Sa = (x - y) * (iR + uR2 + P2R3);
+    const N Sb = (x + y) * (uR2 - iR - P2R3);
+    const N Sg = T(2) * (x * iR - y * uR2 + x * P2R3);
+    const N fa = dexp((Sa - T(1)) * (-two_beta)) * T(-c.alpha);
+    const N fb = dexp((Sb + T(1)) * two_beta) * T(c.alpha);
+    const N ab = fa * fb;
+    const N opab = ab + T(1);
+    const N bma = fb - fa;
+    const N A = x2m1 * dsq(opab) - s2 * dsq(bma);
+    const N B = dsq(xp1 + xm1 * ab) + dsq((y + T(1)) * fa + (T(1) - y) * fb);
+    const N C = x2m1 * opab * (bma - y * (fa + fb)) + s2 * bma * (opab + x * (T(1) - ab));
+    const N psi2 = P2R3 * two_beta;                                            // 2 psi
+    const N g2 = T(c.three_beta2) * dsq(iR3) * (dsq(P3) - dsq(P2)) + (Sg - T(2)) * two_beta; // 2 gamma''
+    const N e2psi = dexp(psi2);
+    const N ie2psi = drcp(e2psi);
+    const N iA = drcp(A);
+    const N iB = drcp(B);
     P.invf = ie2psi * B * iA;
     P.F = e2psi * A * iB * drcp(x2m1 * s2) * T(1.0 / c.k2);
     P.om = ie2psi * C * iA * T(c.two_k) - T(c.w_inf);
@@ -230,8 +273,8 @@ template <class T>
 GT_HD void mn_rates(const SpacetimeC &c, T r, T th, T pr, T pth, T pt, T pph,
                                          Rates<T> &o)
 {
-    MNPot<T> P;
-    mn_potentials(c, r, th, P);
+    MNPot<D3<T>> P;
+    mn_potentials<T, D3<T>>(c, r, th, P);
     const D3<T> pw = P.om * pt + pph;                 // p_phi + w p_t
     const D3<T> H2 = P.invf * (-pt * pt) + P.F * dsq(pw) + P.G * (P.Delta * (pr * pr) + pth * pth);
     const T Fpw = P.F.v * pw.v;
@@ -246,8 +289,8 @@ GT_HD void mn_rates(const SpacetimeC &c, T r, T th, T pr, T pth, T pt, T pph,
 #ifdef __CUDACC__
 __device__ __forceinline__ void mn_upper(const SpacetimeC &c, double r, double th, double g[5])
 {
-    MNPot<double> P;
-    mn_potentials(c, r, th, P);
+    MNPot<V1<double>> P;
+    mn_potentials<double, V1<double>>(c, r, th, P);
     g[0] = -P.invf.v + P.om.v * P.om.v * P.F.v;
     g[1] = P.om.v * P.F.v;
     g[2] = P.F.v;

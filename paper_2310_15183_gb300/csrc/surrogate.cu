@@ -1,0 +1,692 @@
+// surrogate.cu -- the MLP surrogate of the ray tracer: per-pixel (alpha, beta, spin,
+// q, theta0) -> (escape logit, end direction), trained on rays the integrator itself
+// produces, evaluated with the tcgen05 BF16 GEMM, and backed by the integrator for
+// low-confidence and photon-ring pixels.
+//
+// Network: 16 (5 features, zero padded) -> 256 -> 256 -> 256 -> 256 -> 16 (4 used:
+// logit and the unit vector of the end direction, which unlike (theta, phi) has no
+// jump at phi = +-pi), SiLU between layers.  FP32 master weights and AdamW state;
+// BF16 weights and activations feed the tensor cores; accumulation is FP32.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/geotrace.h"
+#include "internal.cuh"
+#include "mlp.cuh"
+#include "camera.cuh"
+#include "surrogate.cuh"
+
+namespace gt {
+namespace sg {
+
+// ------------------------------------------------------------------ kernels
+__device__ __forceinline__ float sigmoidf(float z) { return 1.0f / (1.0f + __expf(-z)); }
+
+// counter-based normal deviates: splitmix64 -> two uniforms -> Box-Muller
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x)
+{
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+__global__ void init_params_kernel(float *p, int64_t n, const int64_t *offs, const float *scales,
+                                   int n_seg, uint64_t seed)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int s = 0;
+    while (s + 1 < n_seg && offs[s + 1] <= i) ++s;
+    const float sc = scales[s];
+    if (sc == 0.0f) {
+        p[i] = 0.0f;
+        return;
+    }
+    const uint64_t a = splitmix64(seed ^ (uint64_t)(2 * i));
+    const uint64_t b = splitmix64(seed ^ (uint64_t)(2 * i + 1));
+    const double u1 = ((a >> 11) + 1) * (1.0 / 9007199254740993.0);
+    const double u2 = (b >> 11) * (1.0 / 9007199254740992.0);
+    p[i] = sc * (float)(sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2));
+}
+
+// features of samples [row0, row0 + n): X0[r, 0..15] (bf16)
+__global__ void features_kernel(int64_t n, int64_t row0, const double *alpha, const double *beta,
+                                const double *spin, const double *q, const double *theta0,
+                                Norm nm, __nv_bfloat16 *X0)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int64_t k = row0 + r;
+    float f[16];
+    f[0] = (float)(alpha[k] * nm.inv_h);
+    f[1] = (float)(beta[k] * nm.inv_v);
+    f[2] = (float)(spin[k] * nm.spin_scale + nm.spin_shift);
+    f[3] = (float)(q[k] * nm.q_scale);
+    f[4] = (float)(theta0[k] * nm.th_scale + nm.th_shift);
+#pragma unroll
+    for (int j = 5; j < 16; j++) f[j] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 16; j++) X0[r * 16 + j] = __float2bfloat16(f[j]);
+}
+
+// features of camera pixels [pix0, pix0 + n) (flat j*res_x + i)
+__global__ void camera_features_kernel(int64_t n, int64_t pix0, const CamDesc *cam, Norm nm,
+                                       __nv_bfloat16 *X0)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const CamDesc &c = *cam;
+    const int64_t pix = pix0 + r;
+    const int i = (int)(pix % c.res_x), j = (int)(pix / c.res_x);
+    const double al = c.res_x > 1 ? c.H * (double)(2 * i - (c.res_x - 1)) / (double)(c.res_x - 1) : 0.0;
+    const double bt = c.res_y > 1 ? c.V * (double)(2 * j - (c.res_y - 1)) / (double)(c.res_y - 1) : 0.0;
+    float f[16];
+    f[0] = (float)(al * nm.inv_h);
+    f[1] = (float)(bt * nm.inv_v);
+    f[2] = (float)((c.S / c.M) / c.M * nm.spin_scale + nm.spin_shift);
+    f[3] = (float)(c.Q * nm.q_scale);
+    f[4] = (float)(c.th0 * nm.th_scale + nm.th_shift);
+#pragma unroll
+    for (int jj = 5; jj < 16; jj++) f[jj] = 0.0f;
+#pragma unroll
+    for (int jj = 0; jj < 16; jj++) X0[r * 16 + jj] = __float2bfloat16(f[jj]);
+}
+
+// Loss of rows [0, B): BCE(logit, y) + w_dir * y * |d_pred - d|^2, averaged over B.
+// labels: [B x 4] = (y, dx, dy, dz).  Writes dZ5 (fp32 and bf16, 16 columns, zeros
+// beyond 4) and accumulates the loss sum.
+__global__ void head_kernel(int B, const float *Z5, const float *labels, float w_dir, float inv_b,
+                            float *dZ5f, __nv_bfloat16 *dZ5b, float *loss_acc)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    float l = 0.0f;
+    if (r < B) {
+        const float *z = Z5 + (int64_t)r * 16;
+        const float *lab = labels + (int64_t)r * 4;
+        const float y = lab[0];
+        const float zl = z[0];
+        // numerically stable BCE with logits
+        l = fmaxf(zl, 0.0f) - zl * y + log1pf(__expf(-fabsf(zl)));
+        float g[16];
+        g[0] = (sigmoidf(zl) - y) * inv_b;
+        for (int j = 1; j < 4; j++) {
+            const float d = z[j] - lab[j];
+            l += w_dir * y * d * d;
+            g[j] = 2.0f * w_dir * y * d * inv_b;
+        }
+        for (int j = 4; j < 16; j++) g[j] = 0.0f;
+        for (int j = 0; j < 16; j++) {
+            dZ5f[(int64_t)r * 16 + j] = g[j];
+            dZ5b[(int64_t)r * 16 + j] = __float2bfloat16(g[j]);
+        }
+    }
+    // warp-reduce the loss, one atomic per warp
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss_acc, l);
+}
+
+// dZ = dX * SiLU'(Z), SiLU'(z) = s (1 + z (1 - s)), s = sigmoid(z)
+__global__ void silu_backward_kernel(int64_t n, const float *dX, const float *Z, float *dZf,
+                                     __nv_bfloat16 *dZb)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float z = Z[i];
+    const float s = sigmoidf(z);
+    const float g = dX[i] * s * (1.0f + z * (1.0f - s));
+    dZf[i] = g;
+    dZb[i] = __float2bfloat16(g);
+}
+
+// out[c] += sum_r M[r, c]  (rows x cols, row-major)
+__global__ void colsum_kernel(const float *Mx, int64_t rows, int cols, float *out)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    const int64_t per = (rows + gridDim.y - 1) / gridDim.y;
+    const int64_t r0 = blockIdx.y * per, r1 = min(rows, r0 + per);
+    float s = 0.0f;
+    for (int64_t r = r0; r < r1; r++) s += Mx[r * cols + c];
+    atomicAdd(&out[c], s);
+}
+
+__global__ void adamw_kernel(int64_t n, float *p, const float *g, float *m, float *v, float lr,
+                             float b1, float b2, float eps, float wd, float bc1, float bc2,
+                             const uint8_t *decay_mask)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    float pi = p[i];
+    if (decay_mask[i]) pi -= lr * wd * pi;
+    pi -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    p[i] = pi;
+}
+
+__global__ void to_bf16_kernel(int64_t n, const float *src, __nv_bfloat16 *dst)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = __float2bfloat16(src[i]);
+}
+
+// Photon-ring test for a Kerr pixel: with E = -p_t, L = p_phi and the Carter constant
+// K of the initial momentum, the radial potential
+//   R(r) = (E (r^2 + a^2) - a L)^2 - Delta ((L - a E)^2 + K)
+// has a (near) double root for rays near the critical curve.  Returns
+// min over r in (r_+, r0] of R(r) / (E^2 r^4) on a geometric grid.
+__device__ double kerr_rmin(const CamDesc &c, const Ray64 &p)
+{
+    const double a = c.st.a, M = c.M;
+    const double E = -p.pt, L = p.pph;
+    const double ct = cos(c.th0), st = sin(c.th0);
+    const double K = p.pth * p.pth + ct * ct * (-a * a * E * E + L * L / (st * st));
+    const double rp = c.st.r_plus;
+    const double lo = log(rp * 1.0001), hi = log(c.r0);
+    double best = 1e300;
+    for (int k = 0; k <= 96; k++) {
+        const double r = exp(lo + (hi - lo) * k / 96.0);
+        const double W = E * (r * r + a * a) - a * L;
+        const double D = r * r - 2.0 * M * r + a * a;
+        const double R = W * W - D * ((L - a * E) * (L - a * E) + K);
+        const double v = R / (E * E * r * r * r * r);
+        best = v < best ? v : best;
+    }
+    return best;
+}
+
+// Decide per pixel: confident surrogate answer, or fall back to the integrator.
+__global__ void gate_kernel(int64_t n, int64_t pix0, const CamDesc *cam, const float *Z5, float tau,
+                            double band, double *t, double *r, double *th, double *ph,
+                            uint8_t *status, uint32_t *nsteps, int64_t *fallback,
+                            unsigned long long *n_fallback)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool fb = false;
+    int64_t pix = pix0 + k;
+    if (k < n) {
+        const float *z = Z5 + k * 16;
+        const float logit = z[0];
+        bool ring = false;
+        if (band > 0.0 && cam->st.kind == KIND_KERR) {
+            Ray64 p;
+            camera_init(*cam, pix, p);
+            ring = fabs(kerr_rmin(*cam, p)) < band;
+        }
+        fb = fabsf(logit) < tau || ring;
+        if (!fb) {
+            if (logit > 0.0f) {
+                const float nx = z[1], ny = z[2], nz = z[3];
+                const float nn = sqrtf(nx * nx + ny * ny + nz * nz);
+                th[pix] = acos(fminf(fmaxf(nz / nn, -1.0f), 1.0f));
+                ph[pix] = atan2(ny, nx);
+                status[pix] = GT_RAY_ESCAPED;
+            } else {
+                th[pix] = nan("");
+                ph[pix] = nan("");
+                status[pix] = GT_RAY_HORIZON;
+            }
+            t[pix] = nan("");
+            r[pix] = nan("");
+            nsteps[pix] = 0;
+        }
+    }
+    // warp-aggregated append of the fallback pixels
+    const unsigned mask = __ballot_sync(0xffffffffu, fb);
+    if (mask) {
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(mask) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(n_fallback, (unsigned long long)__popc(mask));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (fb) fallback[base + __popc(mask & ((1u << lane) - 1u))] = pix;
+    }
+}
+
+} // namespace sg
+} // namespace gt
+
+// ====================================================================== host side
+namespace {
+
+using namespace gt;
+using namespace gt::sg;
+
+__global__ void labels_kernel(int64_t n, int64_t row0, const uint8_t *status, const double *th,
+                              const double *ph, float *lab)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int64_t k = row0 + r;
+    const bool esc = status[k] == GT_RAY_ESCAPED;
+    float y = esc ? 1.0f : 0.0f, dx = 0.f, dy = 0.f, dz = 0.f;
+    if (esc) {
+        const double s = sin(th[k]);
+        dx = (float)(s * cos(ph[k]));
+        dy = (float)(s * sin(ph[k]));
+        dz = (float)cos(th[k]);
+    }
+    lab[r * 4 + 0] = y;
+    lab[r * 4 + 1] = dx;
+    lab[r * 4 + 2] = dy;
+    lab[r * 4 + 3] = dz;
+}
+
+inline unsigned blocks_for(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b); }
+
+} // namespace
+
+struct gt_surrogate {
+    int device = 0;
+    Norm norm = {};
+    int64_t w_off[N_LAYERS] = {}, b_off[N_LAYERS] = {};
+    int64_t n_params = 0;
+    float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr; // fp32 params, grads, Adam
+    uint8_t *decay = nullptr;
+    __nv_bfloat16 *wb = nullptr; // bf16 copy of all params (only weights used)
+    int64_t step = 0;
+    // workspace for `rows` rows
+    int64_t rows = 0;
+    __nv_bfloat16 *X[N_LAYERS] = {}; // inputs of each layer (bf16)
+    float *Z[N_LAYERS] = {};         // pre-activations (fp32)
+    float *dXf = nullptr, *dZf = nullptr, *lab = nullptr, *loss = nullptr;
+    __nv_bfloat16 *dZb = nullptr;
+    int *err = nullptr;
+};
+
+namespace {
+
+void free_ws(gt_surrogate *s)
+{
+    for (int l = 0; l < N_LAYERS; l++) {
+        cudaFree(s->X[l]);
+        cudaFree(s->Z[l]);
+        s->X[l] = nullptr;
+        s->Z[l] = nullptr;
+    }
+    cudaFree(s->dXf);
+    cudaFree(s->dZf);
+    cudaFree(s->dZb);
+    cudaFree(s->lab);
+    s->dXf = s->dZf = s->lab = nullptr;
+    s->dZb = nullptr;
+    s->rows = 0;
+}
+
+int ensure_ws(gt_surrogate *s, int64_t rows)
+{
+    if (s->rows >= rows) return GT_OK;
+    free_ws(s);
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < N_LAYERS && e == cudaSuccess; l++) {
+        e = cudaMalloc(&s->X[l], rows * IN_DIM[l] * sizeof(__nv_bfloat16));
+        if (e == cudaSuccess) e = cudaMalloc(&s->Z[l], rows * OUT_DIM[l] * sizeof(float));
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&s->dXf, rows * 256 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&s->dZf, rows * 256 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&s->dZb, rows * 256 * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMalloc(&s->lab, rows * 4 * sizeof(float));
+    if (e != cudaSuccess) {
+        free_ws(s);
+        return e == cudaErrorMemoryAllocation ? GT_ERR_OOM : GT_ERR_CUDA;
+    }
+    s->rows = rows;
+    return GT_OK;
+}
+
+struct Dev {
+    int prev = -1;
+    bool ok = false;
+    explicit Dev(int d)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(d) == cudaSuccess;
+    }
+    ~Dev()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+cudaError_t gemm(const __nv_bfloat16 *A, int64_t a_sm, int64_t a_sk, const __nv_bfloat16 *B,
+                 int64_t b_sn, int64_t b_sk, int M, int N, int K, const float *bias, int act,
+                 float *pre, float *C32, int64_t ldc, bool atomic, __nv_bfloat16 *C16, int splits,
+                 int *err, cudaStream_t st)
+{
+    GemmArgs g = {};
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.A = A;
+    g.a_sm = a_sm;
+    g.a_sk = a_sk;
+    g.B = B;
+    g.b_sn = b_sn;
+    g.b_sk = b_sk;
+    g.bias = bias;
+    g.act = act;
+    g.pre = pre;
+    g.ld_pre = N;
+    g.C32 = C32;
+    g.ldc = ldc;
+    g.atomic = atomic ? 1 : 0;
+    g.C16 = C16;
+    g.ldc16 = N;
+    g.err = err;
+    const int bn = N >= 256 ? 256 : (N >= 128 ? 128 : (N >= 64 ? 64 : (N >= 32 ? 32 : 16)));
+    return launch_gemm(g, bn, splits, st);
+}
+
+// Forward pass of `B` rows whose features are in X[0]; leaves Z[4] = network output.
+cudaError_t forward(gt_surrogate *s, int B, cudaStream_t st)
+{
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < N_LAYERS && e == cudaSuccess; l++) {
+        const bool last = (l == N_LAYERS - 1);
+        e = gemm(s->X[l], IN_DIM[l], 1, s->wb + s->w_off[l], IN_DIM[l], 1, B, OUT_DIM[l], IN_DIM[l],
+                 s->p + s->b_off[l], last ? 0 : 1, last ? nullptr : s->Z[l],
+                 last ? s->Z[l] : nullptr, OUT_DIM[l], false, last ? nullptr : s->X[l + 1], 1,
+                 s->err, st);
+    }
+    return e;
+}
+
+// Backward pass of B rows with labels in s->lab: gradients (zeroed here) into s->g.
+cudaError_t backward(gt_surrogate *s, int B, float w_dir, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(s->g, 0, s->n_params * sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    head_kernel<<<blocks_for(B), 256, 0, st>>>(B, s->Z[N_LAYERS - 1], s->lab, w_dir, 1.0f / B,
+                                               s->dZf, s->dZb, s->loss);
+    for (int l = N_LAYERS - 1; l >= 0 && e == cudaSuccess; l--) {
+        const int N = OUT_DIM[l], K = IN_DIM[l];
+        // dW_l[n, k] = sum_b dZ[b, n] X_l[b, k]   (split over the batch)
+        const int splits = B >= 4096 ? (B / 2048 < 64 ? B / 2048 : 64) : 1;
+        e = gemm(s->dZb, 1, N, s->X[l], 1, K, N, K, B, nullptr, 0, nullptr, s->g + s->w_off[l], K,
+                 true, nullptr, splits, s->err, st);
+        if (e != cudaSuccess) break;
+        // db_l = column sums of dZ
+        colsum_kernel<<<dim3(blocks_for(N, 128), 64), 128, 0, st>>>(s->dZf, B, N, s->g + s->b_off[l]);
+        if (l == 0) break;
+        // dX[b, k] = sum_n dZ[b, n] W_l[n, k]
+        e = gemm(s->dZb, N, 1, s->wb + s->w_off[l], 1, K, B, K, N, nullptr, 0, nullptr, s->dXf, K,
+                 false, nullptr, 1, s->err, st);
+        if (e != cudaSuccess) break;
+        silu_backward_kernel<<<blocks_for((int64_t)B * K), 256, 0, st>>>((int64_t)B * K, s->dXf,
+                                                                         s->Z[l - 1], s->dZf, s->dZb);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+int check_err(gt_surrogate *s, cudaStream_t st)
+{
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, s->err, sizeof h, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return GT_ERR_CUDA;
+    return h ? GT_ERR_TIMEOUT : GT_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+int gt_surrogate_num_params(int64_t *out)
+{
+    if (!out) return GT_ERR_INVALID_ARG;
+    int64_t n = 0;
+    for (int l = 0; l < N_LAYERS; l++) n += (int64_t)OUT_DIM[l] * IN_DIM[l] + OUT_DIM[l];
+    *out = n;
+    return GT_OK;
+}
+
+int gt_surrogate_create(int device, const gt_surrogate_norm *nrm, uint64_t seed, gt_surrogate **out)
+{
+    if (!out || !nrm) return GT_ERR_INVALID_ARG;
+    if (!(nrm->r0 > 0) || !(nrm->fov_deg > 0 && nrm->fov_deg < 180) || !(nrm->spin_max > 0) ||
+        !(nrm->theta0_max > nrm->theta0_min) || !(nrm->q_max > 0))
+        return GT_ERR_INVALID_ARG;
+    *out = nullptr;
+    Dev d(device);
+    if (!d.ok) return GT_ERR_CUDA;
+    gt_surrogate *s = new (std::nothrow) gt_surrogate();
+    if (!s) return GT_ERR_OOM;
+    s->device = device;
+    const double V = tan(0.5 * nrm->fov_deg / 180.0 * M_PI) / nrm->r0;
+    const double H = atan(tan(V));
+    s->norm.inv_h = 1.0 / H;
+    s->norm.inv_v = 1.0 / V;
+    s->norm.spin_scale = 2.0 / nrm->spin_max;
+    s->norm.spin_shift = -1.0;
+    s->norm.q_scale = 1.0 / nrm->q_max;
+    s->norm.th_scale = 2.0 / (nrm->theta0_max - nrm->theta0_min);
+    s->norm.th_shift = -(nrm->theta0_max + nrm->theta0_min) / (nrm->theta0_max - nrm->theta0_min);
+    int64_t off = 0;
+    std::vector<int64_t> offs;
+    std::vector<float> scales;
+    std::vector<uint8_t> decay;
+    for (int l = 0; l < N_LAYERS; l++) {
+        s->w_off[l] = off;
+        offs.push_back(off);
+        // LeCun-normal weights (the 11 zero-padded input features do not count)
+        const int fan_in = l == 0 ? 5 : IN_DIM[l];
+        scales.push_back((float)(1.0 / sqrt((double)fan_in)));
+        off += (int64_t)OUT_DIM[l] * IN_DIM[l];
+        s->b_off[l] = off;
+        offs.push_back(off);
+        scales.push_back(0.0f);
+        off += OUT_DIM[l];
+    }
+    s->n_params = off;
+    decay.assign(off, 0);
+    for (int l = 0; l < N_LAYERS; l++)
+        for (int64_t i = s->w_off[l]; i < s->b_off[l]; i++) decay[i] = 1;
+    int64_t *d_offs = nullptr;
+    float *d_scales = nullptr;
+    cudaError_t e = cudaMalloc(&s->p, off * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&s->g, off * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&s->m, off * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&s->v, off * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&s->wb, off * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMalloc(&s->decay, off);
+    if (e == cudaSuccess) e = cudaMalloc(&s->loss, sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&s->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&d_offs, offs.size() * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&d_scales, scales.size() * sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(d_offs, offs.data(), offs.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(d_scales, scales.data(), scales.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->decay, decay.data(), off, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(s->m, 0, off * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(s->v, 0, off * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(s->err, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        init_params_kernel<<<blocks_for(off), 256>>>(s->p, off, d_offs, d_scales, (int)offs.size(), seed);
+        to_bf16_kernel<<<blocks_for(off), 256>>>(off, s->p, s->wb);
+        e = cudaDeviceSynchronize();
+    }
+    cudaFree(d_offs);
+    cudaFree(d_scales);
+    if (e != cudaSuccess) {
+        gt_surrogate_destroy(s);
+        return e == cudaErrorMemoryAllocation ? GT_ERR_OOM : GT_ERR_CUDA;
+    }
+    *out = s;
+    return GT_OK;
+}
+
+int gt_surrogate_destroy(gt_surrogate *s)
+{
+    if (!s) return GT_ERR_INVALID_ARG;
+    Dev d(s->device);
+    cudaDeviceSynchronize();
+    free_ws(s);
+    cudaFree(s->p);
+    cudaFree(s->g);
+    cudaFree(s->m);
+    cudaFree(s->v);
+    cudaFree(s->wb);
+    cudaFree(s->decay);
+    cudaFree(s->loss);
+    cudaFree(s->err);
+    delete s;
+    return GT_OK;
+}
+
+int gt_surrogate_get_params(gt_surrogate *s, float *host, int64_t n)
+{
+    if (!s || !host || n != s->n_params) return GT_ERR_INVALID_ARG;
+    Dev d(s->device);
+    return cudaMemcpy(host, s->p, n * sizeof(float), cudaMemcpyDeviceToHost) == cudaSuccess ? GT_OK
+                                                                                           : GT_ERR_CUDA;
+}
+
+int gt_surrogate_set_params(gt_surrogate *s, const float *host, int64_t n)
+{
+    if (!s || !host || n != s->n_params) return GT_ERR_INVALID_ARG;
+    Dev d(s->device);
+    cudaError_t e = cudaMemcpy(s->p, host, n * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        to_bf16_kernel<<<blocks_for(n), 256>>>(n, s->p, s->wb);
+        e = cudaDeviceSynchronize();
+    }
+    return e == cudaSuccess ? GT_OK : GT_ERR_CUDA;
+}
+
+int gt_surrogate_eval(gt_ctx *ctx, gt_surrogate *s, int64_t n, const double *alpha,
+                      const double *beta, const double *spin, const double *q,
+                      const double *theta0, float *out)
+{
+    if (!ctx || !s || n < 0 || !alpha || !beta || !spin || !q || !theta0 || !out)
+        return GT_ERR_INVALID_ARG;
+    Dev d(s->device);
+    cudaStream_t st = gt_internal_stream(ctx);
+    const int64_t chunk = 1 << 18;
+    int rc = ensure_ws(s, n < chunk ? (n > 0 ? n : 1) : chunk);
+    if (rc != GT_OK) return rc;
+    for (int64_t r0 = 0; r0 < n; r0 += chunk) {
+        const int64_t B = n - r0 < chunk ? n - r0 : chunk;
+        features_kernel<<<blocks_for(B), 256, 0, st>>>(B, r0, alpha, beta, spin, q, theta0, s->norm,
+                                                       s->X[0]);
+        cudaError_t e = forward(s, (int)B, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(out + r0 * 4, 4 * sizeof(float), s->Z[N_LAYERS - 1], 16 * sizeof(float),
+                                  4 * sizeof(float), B, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return GT_ERR_CUDA;
+    }
+    return check_err(s, st);
+}
+
+int gt_surrogate_grad(gt_ctx *ctx, gt_surrogate *s, int64_t n, const double *alpha,
+                      const double *beta, const double *spin, const double *q,
+                      const double *theta0, const uint8_t *status, const double *th_end,
+                      const double *ph_end, float dir_weight, float *grads_host, float *loss_host)
+{
+    if (!ctx || !s || n < 1 || n > (1 << 20) || !grads_host || !loss_host) return GT_ERR_INVALID_ARG;
+    Dev d(s->device);
+    cudaStream_t st = gt_internal_stream(ctx);
+    int rc = ensure_ws(s, n);
+    if (rc != GT_OK) return rc;
+    features_kernel<<<blocks_for(n), 256, 0, st>>>(n, 0, alpha, beta, spin, q, theta0, s->norm, s->X[0]);
+    labels_kernel<<<blocks_for(n), 256, 0, st>>>(n, 0, status, th_end, ph_end, s->lab);
+    cudaError_t e = cudaMemsetAsync(s->loss, 0, sizeof(float), st);
+    if (e == cudaSuccess) e = forward(s, (int)n, st);
+    if (e == cudaSuccess) e = backward(s, (int)n, dir_weight, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(grads_host, s->g, s->n_params * sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(loss_host, s->loss, sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return GT_ERR_CUDA;
+    rc = check_err(s, st);
+    if (rc == GT_OK) *loss_host /= (float)n;
+    return rc;
+}
+
+int gt_surrogate_train(gt_ctx *ctx, gt_surrogate *s, const gt_train_cfg *cfg, int64_t n,
+                       const double *alpha, const double *beta, const double *spin,
+                       const double *q, const double *theta0, const uint8_t *status,
+                       const double *th_end, const double *ph_end, float *loss_per_epoch)
+{
+    if (!ctx || !s || !cfg || n < 1 || cfg->epochs < 1 || cfg->batch < 128 || cfg->batch % 128 ||
+        cfg->batch > (1 << 20) || !(cfg->lr > 0))
+        return GT_ERR_INVALID_ARG;
+    Dev d(s->device);
+    cudaStream_t st = gt_internal_stream(ctx);
+    const int B = cfg->batch;
+    int rc = ensure_ws(s, B);
+    if (rc != GT_OK) return rc;
+    const int64_t nb = n / B; // full batches only
+    if (nb < 1) return GT_ERR_INVALID_ARG;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    for (int ep = 0; ep < cfg->epochs; ep++) {
+        cudaError_t e = cudaMemsetAsync(s->loss, 0, sizeof(float), st);
+        // cosine learning-rate schedule over the whole run
+        for (int64_t b = 0; b < nb && e == cudaSuccess; b++) {
+            const double prog = ((double)ep * nb + b) / ((double)cfg->epochs * nb);
+            const float lr = (float)(cfg->lr * 0.5 * (1.0 + cos(M_PI * prog)));
+            features_kernel<<<blocks_for(B), 256, 0, st>>>(B, b * B, alpha, beta, spin, q, theta0,
+                                                           s->norm, s->X[0]);
+            labels_kernel<<<blocks_for(B), 256, 0, st>>>(B, b * B, status, th_end, ph_end, s->lab);
+            e = forward(s, B, st);
+            if (e == cudaSuccess) e = backward(s, B, (float)cfg->dir_weight, st);
+            if (e != cudaSuccess) break;
+            s->step++;
+            const float bc1 = 1.0f - powf(b1, (float)s->step), bc2 = 1.0f - powf(b2, (float)s->step);
+            adamw_kernel<<<blocks_for(s->n_params), 256, 0, st>>>(s->n_params, s->p, s->g, s->m, s->v,
+                                                                  lr, b1, b2, eps,
+                                                                  (float)cfg->weight_decay, bc1, bc2,
+                                                                  s->decay);
+            to_bf16_kernel<<<blocks_for(s->n_params), 256, 0, st>>>(s->n_params, s->p, s->wb);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) return GT_ERR_CUDA;
+        if (loss_per_epoch) {
+            float l = 0;
+            e = cudaMemcpyAsync(&l, s->loss, sizeof l, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return GT_ERR_CUDA;
+            loss_per_epoch[ep] = l / (float)(nb * B);
+        }
+    }
+    return check_err(s, st);
+}
+
+} // extern "C"
+
+// Inference with gating (declared in geotrace.h); needs the context's camera, so it is
+// implemented next to the context in capi.cu through these helpers.
+namespace gt {
+namespace sg {
+
+int infer_chunks(gt_surrogate *s, const CamDesc *d_cam, int64_t n_pix, float tau, double band,
+                 double *t, double *r, double *th, double *ph, uint8_t *status, uint32_t *nsteps,
+                 int64_t *d_fallback, unsigned long long *d_nfb, cudaStream_t st)
+{
+    const int64_t chunk = 1 << 19;
+    int rc = ensure_ws(s, n_pix < chunk ? n_pix : chunk);
+    if (rc != GT_OK) return rc;
+    for (int64_t p0 = 0; p0 < n_pix; p0 += chunk) {
+        const int64_t B = n_pix - p0 < chunk ? n_pix - p0 : chunk;
+        camera_features_kernel<<<blocks_for(B), 256, 0, st>>>(B, p0, d_cam, s->norm, s->X[0]);
+        cudaError_t e = forward(s, (int)B, st);
+        if (e != cudaSuccess) return GT_ERR_CUDA;
+        gate_kernel<<<blocks_for(B), 256, 0, st>>>(B, p0, d_cam, s->Z[N_LAYERS - 1], tau, band, t, r,
+                                                   th, ph, status, nsteps, d_fallback, d_nfb);
+        if (cudaGetLastError() != cudaSuccess) return GT_ERR_CUDA;
+    }
+    return check_err(s, st);
+}
+
+} // namespace sg
+} // namespace gt

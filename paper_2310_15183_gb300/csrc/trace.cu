@@ -22,6 +22,7 @@
 #include <stdint.h>
 
 #include "../../include/geotrace.h"
+#include "camera.cuh"
 #include "internal.cuh"
 #include "spacetime.cuh"
 
@@ -113,46 +114,6 @@ cudaError_t launch_camera_setup(CamDesc *d_cams, int n_cams, int flags, double r
     camera_setup_kernel<<<(n_cams + block - 1) / block, block, 0, s>>>(d_cams, n_cams, flags,
                                                                        r_switch);
     return cudaGetLastError();
-}
-
-// ------------------------------------------------------------------ ray state
-struct Ray64 {
-    double t, r, th, ph, pr, pth; // evolving
-    double pt, pph;               // constants of motion
-};
-
-// Initial data of pixel `local` of camera `c` (Sec. 3.3.1, listing's camera block):
-// v = (T, -1, beta_j, alpha_i / sin theta0), T the root (-B + sqrt(B^2 - 4AC))/(2A)
-// of g(v, v) = 0, v /= |T|, p = g v at (0, r0, theta0, 0).
-__device__ __forceinline__ void camera_init_dir(const CamDesc &c, double al, double bt, Ray64 &x)
-{
-    double vr = -1.0, vth = bt, vph = al * c.inv_sin_th0;
-    const double A = c.gl_tt;
-    const double B = 2.0 * c.gl_tph * vph;
-    const double C = c.gl_rr * vr * vr + c.gl_thth * vth * vth + c.gl_phph * vph * vph;
-    const double T = (-B + sqrt(B * B - 4.0 * A * C)) / (2.0 * A);
-    const double sc = 1.0 / fabs(T);
-    const double vt = T * sc;
-    vr *= sc;
-    vth *= sc;
-    vph *= sc;
-    x.t = 0.0;
-    x.r = c.r0;
-    x.th = c.th0;
-    x.ph = 0.0;
-    x.pt = c.gl_tt * vt + c.gl_tph * vph;
-    x.pr = c.gl_rr * vr;
-    x.pth = c.gl_thth * vth;
-    x.pph = c.gl_tph * vt + c.gl_phph * vph;
-}
-
-__device__ __forceinline__ void camera_init(const CamDesc &c, int64_t local, Ray64 &x)
-{
-    const int i = (int)(local % c.res_x);
-    const int j = (int)(local / c.res_x);
-    const double al = c.res_x > 1 ? c.H * (double)(2 * i - (c.res_x - 1)) / (double)(c.res_x - 1) : 0.0;
-    const double bt = c.res_y > 1 ? c.V * (double)(2 * j - (c.res_y - 1)) / (double)(c.res_y - 1) : 0.0;
-    camera_init_dir(c, al, bt, x);
 }
 
 template <int KIND>
@@ -350,7 +311,38 @@ __device__ __forceinline__ void reproject_pr(const SpacetimeC &st, Ray64 &x)
 }
 
 // ------------------------------------------------------------------ the kernel
-// MODE 0: FP64 plain.  MODE 1: FP32-mixed.  KIND: 0 Kerr, 1 MN, 2 per-camera.
+// MODE 0: FP64 plain.
+// MODE 1: FP32-mixed with the FP64 zone inline (used where no park lists exist).
+// MODE 2: FP32-mixed, FP32 steps only; a ray entering the FP64 zone (r < r_switch) is
+//         parked on the output list; input list items continue in FP32.
+// MODE 3: FP64 zone steps for parked rays; a ray leaving the zone (r > 1.25 r_switch)
+//         is parked on the output list for the next FP32 launch.
+// KIND: 0 Kerr, 1 Manko-Novikov, 2 per-camera.
+// Work of a launch: fresh rays [0, n_fresh) then input-list items [0, *in_count).
+
+__device__ __forceinline__ void park(const TraceArgs &A, int64_t id, uint32_t n, int cam,
+                                     const Ray64 &x, bool *ok)
+{
+    const unsigned long long slot = atomicAdd(A.out_count, 1ull);
+    if (slot >= A.out_cap) { // cannot happen with capacity = rays of the launch
+        *ok = false;
+        return;
+    }
+    ParkItem &it = A.out_items[slot];
+    it.id = id;
+    it.n = n;
+    it.cam = cam;
+    it.t = x.t;
+    it.r = x.r;
+    it.th = x.th;
+    it.ph = x.ph;
+    it.pr = x.pr;
+    it.pth = x.pth;
+    it.pt = x.pt;
+    it.pph = x.pph;
+    *ok = true;
+}
+
 template <int MODE, int KIND>
 __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A, int one_shot)
 {
@@ -360,6 +352,9 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A, int one_shot)
     volatile unsigned long long *tflag = A.scratch + SCR_TIMEOUT;
     const uint64_t t_start = A.timeout_ns ? globaltimer_ns() : 0;
     const CamDesc *__restrict__ cams = A.cams;
+    const int64_t n_in =
+        A.in_count ? (int64_t)(*A.in_count < A.in_cap ? *A.in_count : A.in_cap) : 0;
+    const int64_t n_work = A.n_fresh + n_in;
 
     int64_t id = -1;
     int cam = 0;
@@ -372,53 +367,88 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A, int one_shot)
     double r_esc = cams[0].r_escape;
     double r_sw = cams[0].r_switch;
     const float spf = (float)A.sp, w6f = (float)A.w6;
+    const float h_thr_f = (float)(A.sp * 0.00003);
+    F2 r_esc_f = f2_from(r_esc);
+    float r_sw_f = (float)r_sw;
 
-    // Start ray `rid`; returns false (ray already written) when n_steps == 0.
-    auto start = [&](int64_t rid) -> bool {
-        id = rid;
-        if (A.rays) { // per-ray spacetime and camera (surrogate training data)
-            CamDesc d;
-            d.M = A.rays->M;
-            d.S = A.rays->spin[rid] * A.rays->M;
-            d.Q = A.rays->q[rid];
-            d.r0 = A.rays->r0;
-            d.th0 = A.rays->theta0[rid];
-            d.fov_deg = 90.0;
-            d.res_x = d.res_y = 1;
-            d.offset = 0;
-            setup_desc(d, A.flags, A.rays->r_switch);
-            st = d.st;
-            r_esc = d.r_escape;
-            r_sw = d.r_switch;
-            camera_init_dir(d, A.rays->alpha[rid], A.rays->beta[rid], x);
-            n = 0;
-            if (!d.valid || A.n_steps <= 0) {
-                store_ray(A, rid, x.t, x.r, x.th, x.ph, d.valid ? GT_RAY_MAXSTEPS : GT_RAY_NONFINITE, 0);
-                return false;
+    auto load_camera = [&](int c) {
+        cam = c;
+        st = cams[c].st;
+        r_esc = cams[c].r_escape;
+        r_sw = cams[c].r_switch;
+        if (MODE == 2) {
+            r_esc_f = f2_from(r_esc);
+            r_sw_f = (float)r_sw;
+        }
+    };
+    auto load_rayparams = [&](int64_t rid, bool init) {
+        CamDesc d;
+        d.M = A.rays->M;
+        d.S = A.rays->spin[rid] * A.rays->M;
+        d.Q = A.rays->q[rid];
+        d.r0 = A.rays->r0;
+        d.th0 = A.rays->theta0[rid];
+        d.fov_deg = 90.0;
+        d.res_x = d.res_y = 1;
+        d.offset = 0;
+        setup_desc(d, A.flags, A.rays->r_switch);
+        st = d.st;
+        r_esc = d.r_escape;
+        r_sw = d.r_switch;
+        if (MODE == 2) {
+            r_esc_f = f2_from(r_esc);
+            r_sw_f = (float)r_sw;
+        }
+        if (init) camera_init_dir(d, A.rays->alpha[rid], A.rays->beta[rid], x);
+        return d.valid != 0;
+    };
+
+    // Start work item `w`; returns false when the ray is already finished and stored.
+    auto start = [&](int64_t w) -> bool {
+        if (w < A.n_fresh) { // a fresh ray: initial data from the camera
+            const int64_t pix = A.fresh_ids ? A.fresh_ids[w] : w;
+            id = pix;
+            if (A.rays) {
+                const bool valid = load_rayparams(pix, true);
+                n = 0;
+                if (!valid || A.n_steps <= 0) {
+                    store_ray(A, pix, x.t, x.r, x.th, x.ph, valid ? GT_RAY_MAXSTEPS : GT_RAY_NONFINITE, 0);
+                    return false;
+                }
+            } else {
+                if (KIND == 2 || A.n_cams > 1) load_camera(find_camera(cams, A.n_cams, pix));
+                camera_init(cams[cam], A.first + pix - cams[cam].offset, x);
+                n = 0;
+                if (A.n_steps <= 0) {
+                    store_ray(A, pix, x.t, x.r, x.th, x.ph, GT_RAY_MAXSTEPS, 0);
+                    return false;
+                }
             }
-            if (MODE == 1) mixed_from64(x, m);
-            return true;
+        } else { // a parked ray from the input list
+            const ParkItem &it = A.in_items[w - A.n_fresh];
+            id = it.id;
+            n = it.n;
+            if (A.rays)
+                load_rayparams(id, false);
+            else if (KIND == 2 || A.n_cams > 1)
+                load_camera(it.cam);
+            x.t = it.t;
+            x.r = it.r;
+            x.th = it.th;
+            x.ph = it.ph;
+            x.pr = it.pr;
+            x.pth = it.pth;
+            x.pt = it.pt;
+            x.pph = it.pph;
         }
-        if (KIND == 2 || A.n_cams > 1) {
-            cam = find_camera(cams, A.n_cams, rid);
-            st = cams[cam].st;
-            r_esc = cams[cam].r_escape;
-            r_sw = cams[cam].r_switch;
-        }
-        camera_init(cams[cam], A.first + rid - cams[cam].offset, x);
-        n = 0;
-        if (A.n_steps <= 0) {
-            store_ray(A, rid, x.t, x.r, x.th, x.ph, GT_RAY_MAXSTEPS, 0);
-            return false;
-        }
-        if (MODE == 1) mixed_from64(x, m);
+        if (MODE == 1 || MODE == 2) mixed_from64(x, m);
         return true;
     };
 
     if (one_shot) {
         drained = true;
-        const int64_t rid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-        if (rid < A.n_rays) active = start(rid);
+        const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        if (w < n_work) active = start(w);
     }
 
     for (uint32_t it = 0;; ++it) {
@@ -431,10 +461,10 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A, int one_shot)
                 unsigned long long base = 0;
                 if (lane == leader) base = atomicAdd(next, (unsigned long long)cnt);
                 base = __shfl_sync(FULL_MASK, base, leader);
-                if (base + (unsigned long long)cnt >= (unsigned long long)A.n_rays) drained = true;
+                if (base + (unsigned long long)cnt >= (unsigned long long)n_work) drained = true;
                 if (!active) {
-                    const int64_t rid = (int64_t)base + __popc(need & lt_mask);
-                    if (rid < A.n_rays) active = start(rid);
+                    const int64_t w = (int64_t)base + __popc(need & lt_mask);
+                    if (w < n_work) active = start(w);
                 }
             }
         }
@@ -456,7 +486,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A, int one_shot)
             stop = __shfl_sync(FULL_MASK, stop, 0);
             if (stop) {
                 if (active) {
-                    if (MODE == 1) mixed_to64(m, x);
+                    if (MODE == 1 || MODE == 2) mixed_to64(m, x);
                     store_ray(A, id, x.t, x.r, x.th, x.ph, GT_RAY_TIMEOUT, n);
                 }
                 if (!one_shot) {
@@ -464,11 +494,19 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A, int one_shot)
                         unsigned long long base = 0;
                         if (lane == 0) base = atomicAdd(next, 32ull);
                         base = __shfl_sync(FULL_MASK, base, 0);
-                        if (base >= (unsigned long long)A.n_rays) break;
-                        const int64_t rid = (int64_t)base + lane;
-                        if (rid < A.n_rays) {
-                            const int c = A.n_cams > 1 ? find_camera(cams, A.n_cams, rid) : 0;
-                            store_ray(A, rid, 0.0, cams[c].r0, cams[c].th0, 0.0, GT_RAY_TIMEOUT, 0);
+                        if (base >= (unsigned long long)n_work) break;
+                        const int64_t w = (int64_t)base + lane;
+                        if (w < n_work) {
+                            if (w < A.n_fresh) {
+                                const int64_t pix = A.fresh_ids ? A.fresh_ids[w] : w;
+                                const int c = A.n_cams > 1 ? find_camera(cams, A.n_cams, pix) : 0;
+                                const double r0 = A.rays ? A.rays->r0 : cams[c].r0;
+                                const double th0 = A.rays ? A.rays->theta0[pix] : cams[c].th0;
+                                store_ray(A, pix, 0.0, r0, th0, 0.0, GT_RAY_TIMEOUT, 0);
+                            } else {
+                                const ParkItem &p = A.in_items[w - A.n_fresh];
+                                store_ray(A, p.id, p.t, p.r, p.th, p.ph, GT_RAY_TIMEOUT, p.n);
+                            }
                         }
                     }
                 }
@@ -479,7 +517,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A, int one_shot)
 
         // ---- one RK4 step
         int status = -1;
-        if (MODE == 0) {
+        if (MODE == 0 || MODE == 3) {
             Ray64 y;
             const double h = rk4_step64<KIND>(st, x, A.sp, A.w6, y);
             ++n;
@@ -488,11 +526,16 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A, int one_shot)
             } else {
                 x = y;
                 status = exit_status(x.r, h, r_esc, A.sp, n, A.n_steps);
+                if (MODE == 3 && status < 0 && x.r > 1.25 * r_sw) { // leave the FP64 zone
+                    bool ok;
+                    park(A, id, n, cam, x, &ok);
+                    if (ok) active = false;
+                }
             }
-        } else {
+        } else if (MODE == 1) {
             double h;
             bool ok = true;
-            if ((double)m.r.hi < r_sw) { // FP64 zone (near the horizon / photon orbits)
+            if ((double)m.r.hi < r_sw) { // FP64 zone inline
                 Ray64 y;
                 mixed_to64(m, x);
                 h = rk4_step64<KIND>(st, x, A.sp, A.w6, y);
@@ -520,6 +563,33 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A, int one_shot)
                     m.pr = f2_from(x.pr);
                 }
             }
+        } else { // MODE 2: FP32 steps only, exit tests in FP32
+            RayMixed keep = m;
+            const float h = rk4_step32<KIND>(st, m, spf, w6f);
+            ++n;
+            const bool ok = isfinite(h) && isfinite(m.t.hi) && isfinite(m.r.hi) &&
+                            isfinite(m.th.hi) && isfinite(m.ph.hi) && isfinite(m.pr.hi) &&
+                            isfinite(m.pth.hi);
+            if (!ok) {
+                m = keep;
+                status = GT_RAY_NONFINITE;
+            } else if (m.r.hi > r_esc_f.hi || (m.r.hi == r_esc_f.hi && m.r.lo > r_esc_f.lo)) {
+                status = GT_RAY_ESCAPED;
+            } else if (h < h_thr_f) {
+                status = GT_RAY_HORIZON;
+            } else if ((int64_t)n >= A.n_steps) {
+                status = GT_RAY_MAXSTEPS;
+            } else if (m.r.hi < r_sw_f) { // enter the FP64 zone: hand the ray over
+                mixed_to64(m, x);
+                bool parked;
+                park(A, id, n, cam, x, &parked);
+                if (parked) active = false;
+            } else if (A.reproject_every > 0 && (n % (uint32_t)A.reproject_every) == 0u) {
+                mixed_to64(m, x);
+                reproject_pr(st, x);
+                m.pr = f2_from(x.pr);
+            }
+            if (status >= 0) mixed_to64(m, x);
         }
         if (status >= 0) {
             store_ray(A, id, x.t, x.r, x.th, x.ph, status, n);
@@ -535,6 +605,27 @@ static cudaError_t launch_one(const TraceArgs &a, int block, int grid, bool one_
     return cudaGetLastError();
 }
 
+template <int MODE>
+static cudaError_t launch_mode(const TraceArgs &a, int kind_hint, int block, int grid,
+                               bool one_shot, cudaStream_t s)
+{
+    if (kind_hint == KIND_KERR) return launch_one<MODE, KIND_KERR>(a, block, grid, one_shot, s);
+    if (kind_hint == KIND_MN) return launch_one<MODE, KIND_MN>(a, block, grid, one_shot, s);
+    return launch_one<MODE, 2>(a, block, grid, one_shot, s);
+}
+
+cudaError_t launch_trace(const TraceArgs &a, int kmode, int kind_hint, int block, int grid,
+                         bool one_shot, cudaStream_t s)
+{
+    switch (kmode) {
+    case KMODE_FP64: return launch_mode<0>(a, kind_hint, block, grid, one_shot, s);
+    case KMODE_MIXED_INLINE: return launch_mode<1>(a, kind_hint, block, grid, one_shot, s);
+    case KMODE_MIXED_FP32: return launch_mode<2>(a, kind_hint, block, grid, one_shot, s);
+    case KMODE_ZONE_FP64: return launch_mode<3>(a, kind_hint, block, grid, one_shot, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 template <int MODE, int KIND>
 static int occupancy_one(int block)
 {
@@ -545,29 +636,23 @@ static int occupancy_one(int block)
     return n > 0 ? n : 1;
 }
 
-int max_blocks_per_sm(int mode, int kind_hint, int block)
+template <int MODE>
+static int occupancy_mode(int kind_hint, int block)
 {
-    if (mode == GT_MODE_FP64) {
-        if (kind_hint == KIND_KERR) return occupancy_one<0, KIND_KERR>(block);
-        if (kind_hint == KIND_MN) return occupancy_one<0, KIND_MN>(block);
-        return occupancy_one<0, 2>(block);
-    }
-    if (kind_hint == KIND_KERR) return occupancy_one<1, KIND_KERR>(block);
-    if (kind_hint == KIND_MN) return occupancy_one<1, KIND_MN>(block);
-    return occupancy_one<1, 2>(block);
+    if (kind_hint == KIND_KERR) return occupancy_one<MODE, KIND_KERR>(block);
+    if (kind_hint == KIND_MN) return occupancy_one<MODE, KIND_MN>(block);
+    return occupancy_one<MODE, 2>(block);
 }
 
-cudaError_t launch_trace(const TraceArgs &a, int mode, int kind_hint, int block, int grid,
-                         bool one_shot, cudaStream_t s)
+int max_blocks_per_sm(int kmode, int kind_hint, int block)
 {
-    if (mode == GT_MODE_FP64) {
-        if (kind_hint == KIND_KERR) return launch_one<0, KIND_KERR>(a, block, grid, one_shot, s);
-        if (kind_hint == KIND_MN) return launch_one<0, KIND_MN>(a, block, grid, one_shot, s);
-        return launch_one<0, 2>(a, block, grid, one_shot, s);
+    switch (kmode) {
+    case KMODE_FP64: return occupancy_mode<0>(kind_hint, block);
+    case KMODE_MIXED_INLINE: return occupancy_mode<1>(kind_hint, block);
+    case KMODE_MIXED_FP32: return occupancy_mode<2>(kind_hint, block);
+    case KMODE_ZONE_FP64: return occupancy_mode<3>(kind_hint, block);
+    default: return 1;
     }
-    if (kind_hint == KIND_KERR) return launch_one<1, KIND_KERR>(a, block, grid, one_shot, s);
-    if (kind_hint == KIND_MN) return launch_one<1, KIND_MN>(a, block, grid, one_shot, s);
-    return launch_one<1, 2>(a, block, grid, one_shot, s);
 }
 
 } // namespace gt

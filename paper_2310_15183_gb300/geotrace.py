@@ -21,12 +21,16 @@ ERRORS = {-1: "invalid argument", -2: "not configured", -3: "CUDA error", -4: "o
           -5: "device watchdog timeout", -6: "unsupported device or feature"}
 ESCAPED, HORIZON, MAXSTEPS, NONFINITE, TIMEOUT = 0, 1, 2, 3, 4
 MODE_FP64, MODE_FP32_MIXED = 0, 1
-FLAG_COMPAT_WEIGHTS, FLAG_COMPAT_CAMERA, FLAG_ONE_SHOT = 1, 2, 4
+FLAG_COMPAT_WEIGHTS, FLAG_COMPAT_CAMERA, FLAG_ONE_SHOT, FLAG_GRAPH = 1, 2, 4, 8
 
 # every symbol include/geotrace.h declares
 EXPORTS = ("gt_create", "gt_destroy", "gt_set_stream", "gt_set_spacetime", "gt_set_camera",
            "gt_set_options", "gt_trace", "gt_trace_range", "gt_trace_host", "gt_trace_batch", "gt_sync",
-           "gt_device_sm_count", "gt_measure_fma_peak", "gt_gemm_bf16", "gt_strerror")
+           "gt_device_sm_count", "gt_measure_fma_peak", "gt_gemm_bf16",
+           "gt_trace_rays", "gt_autotune", "gt_surrogate_num_params", "gt_surrogate_create",
+           "gt_surrogate_destroy", "gt_surrogate_get_params", "gt_surrogate_set_params",
+           "gt_surrogate_eval", "gt_surrogate_grad", "gt_surrogate_train", "gt_surrogate_infer",
+           "gt_strerror")
 
 
 class GeotraceError(RuntimeError):
@@ -39,6 +43,17 @@ class Options(ctypes.Structure):
     _fields_ = [("block_size", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
                 ("flags", ctypes.c_int), ("reproject_every", ctypes.c_int),
                 ("r_switch", ctypes.c_double), ("timeout_seconds", ctypes.c_double)]
+
+
+class SurrogateNorm(ctypes.Structure):
+    _fields_ = [("r0", ctypes.c_double), ("fov_deg", ctypes.c_double),
+                ("spin_max", ctypes.c_double), ("q_max", ctypes.c_double),
+                ("theta0_min", ctypes.c_double), ("theta0_max", ctypes.c_double)]
+
+
+class TrainCfg(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_double),
+                ("weight_decay", ctypes.c_double), ("dir_weight", ctypes.c_double)]
 
 
 class CameraDesc(ctypes.Structure):
@@ -77,6 +92,20 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.gt_measure_fma_peak.argtypes = [i, i, i, ctypes.POINTER(d)]
     lib.gt_gemm_bf16.argtypes = [i, vp, i, i, i, vp, i64, i64, vp, i64, i64, vp, i, vp, i64,
                                  i, i, i]
+    lib.gt_autotune.argtypes = [vp, i, i64, i64, d, ctypes.c_char_p, ctypes.POINTER(i),
+                                ctypes.POINTER(i), ctypes.POINTER(d)]
+    lib.gt_trace_rays.argtypes = [vp, i64] + [vp] * 5 + [d, d, i64, d, i] + out6
+    lib.gt_surrogate_num_params.argtypes = [ctypes.POINTER(i64)]
+    lib.gt_surrogate_create.argtypes = [i, ctypes.POINTER(SurrogateNorm), ctypes.c_uint64,
+                                        ctypes.POINTER(vp)]
+    lib.gt_surrogate_destroy.argtypes = [vp]
+    lib.gt_surrogate_get_params.argtypes = [vp, vp, i64]
+    lib.gt_surrogate_set_params.argtypes = [vp, vp, i64]
+    lib.gt_surrogate_eval.argtypes = [vp, vp, i64] + [vp] * 5 + [vp]
+    lib.gt_surrogate_grad.argtypes = [vp, vp, i64] + [vp] * 8 + [ctypes.c_float, vp, vp]
+    lib.gt_surrogate_train.argtypes = [vp, vp, ctypes.POINTER(TrainCfg), i64] + [vp] * 8 + [vp]
+    lib.gt_surrogate_infer.argtypes = [vp, vp, ctypes.c_float, d, i64, d, i] + out6 + [
+        ctypes.POINTER(i64)]
     lib.gt_strerror.argtypes = [i]
     lib.gt_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -216,5 +245,110 @@ class Tracer:
         _check(rc, "gt_trace_batch")
         return out
 
+    def autotune(self, mode: int, trial_rays: int = 1 << 17, trial_steps: int = 400,
+                 step_precision: float = 1.5e-4, cache_path: Optional[str] = None):
+        """gt_autotune: returns (block_size, blocks_per_sm, trial steps/s) and keeps them."""
+        b, k, v = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _check(self.lib.gt_autotune(self.ctx, int(mode), int(trial_rays), int(trial_steps),
+                                    float(step_precision),
+                                    cache_path.encode() if cache_path else None,
+                                    ctypes.byref(b), ctypes.byref(k), ctypes.byref(v)),
+               "gt_autotune")
+        return b.value, k.value, v.value
+
+    def trace_rays(self, alpha, beta, spin, q, theta0, M: float, r0: float, n_steps: int,
+                   step_precision: float, mode: int = MODE_FP32_MIXED,
+                   out: Optional[dict] = None) -> dict:
+        """gt_trace_rays: one spacetime and camera per ray (float64 device tensors)."""
+        n = alpha.numel()
+        if out is None:
+            out = self.alloc_outputs(n)
+        rc = self.lib.gt_trace_rays(self.ctx, n, *[_ptr(x) for x in (alpha, beta, spin, q, theta0)],
+                                    float(M), float(r0), int(n_steps), float(step_precision),
+                                    int(mode), *[_ptr(out.get(k)) for k in
+                                                 ("t", "r", "th", "ph", "status", "nsteps")])
+        _check(rc, "gt_trace_rays")
+        return out
+
     def sync(self):
         _check(self.lib.gt_sync(self.ctx), "gt_sync")
+
+
+class Surrogate:
+    """The surrogate network (gt_surrogate_*): training and gated inference."""
+
+    def __init__(self, device: int = 0, r0: float = 15.0, fov_deg: float = 75.0,
+                 spin_max: float = 0.99, q_max: float = 2.0, theta0_min: float = 0.0872664626,
+                 theta0_max: float = 1.5707963268, seed: int = 1):
+        self.lib = load_library()
+        self.device = device
+        self.norm = SurrogateNorm(r0, fov_deg, spin_max, q_max, theta0_min, theta0_max)
+        h = ctypes.c_void_p()
+        _check(self.lib.gt_surrogate_create(device, ctypes.byref(self.norm), seed, ctypes.byref(h)),
+               "gt_surrogate_create")
+        self.h = h
+        n = ctypes.c_int64()
+        _check(self.lib.gt_surrogate_num_params(ctypes.byref(n)), "gt_surrogate_num_params")
+        self.n_params = n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gt_surrogate_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.n_params, dtype=np.float32)
+        _check(self.lib.gt_surrogate_get_params(self.h, out.ctypes.data, self.n_params),
+               "gt_surrogate_get_params")
+        return out
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(self.lib.gt_surrogate_set_params(self.h, p.ctypes.data, p.size),
+               "gt_surrogate_set_params")
+
+    def eval(self, tracer: "Tracer", inputs) -> "object":
+        import torch
+        n = inputs[0].numel()
+        out = torch.empty(n, 4, dtype=torch.float32, device=inputs[0].device)
+        _check(self.lib.gt_surrogate_eval(tracer.ctx, self.h, n, *[_ptr(x) for x in inputs],
+                                          _ptr(out)), "gt_surrogate_eval")
+        return out
+
+    def grad(self, tracer: "Tracer", inputs, labels, dir_weight: float):
+        n = inputs[0].numel()
+        g = np.empty(self.n_params, dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(self.lib.gt_surrogate_grad(tracer.ctx, self.h, n, *[_ptr(x) for x in inputs],
+                                          *[_ptr(x) for x in labels], float(dir_weight),
+                                          g.ctypes.data, ctypes.byref(loss)), "gt_surrogate_grad")
+        return g, loss.value
+
+    def train(self, tracer: "Tracer", inputs, labels, epochs: int, batch: int, lr: float,
+              weight_decay: float = 0.0, dir_weight: float = 10.0) -> np.ndarray:
+        n = inputs[0].numel()
+        cfg = TrainCfg(epochs, batch, lr, weight_decay, dir_weight)
+        losses = np.zeros(epochs, dtype=np.float32)
+        _check(self.lib.gt_surrogate_train(tracer.ctx, self.h, ctypes.byref(cfg), n,
+                                           *[_ptr(x) for x in inputs], *[_ptr(x) for x in labels],
+                                           losses.ctypes.data), "gt_surrogate_train")
+        return losses
+
+    def infer(self, tracer: "Tracer", tau: float, band: float, n_steps: int,
+              step_precision: float, mode: int = MODE_FP32_MIXED, out: Optional[dict] = None):
+        n = tracer.res[0] * tracer.res[1]
+        if out is None:
+            out = tracer.alloc_outputs(n)
+        nfb = ctypes.c_int64()
+        _check(self.lib.gt_surrogate_infer(tracer.ctx, self.h, float(tau), float(band),
+                                           int(n_steps), float(step_precision), int(mode),
+                                           *[_ptr(out[k]) for k in ("t", "r", "th", "ph",
+                                                                    "status", "nsteps")],
+                                           ctypes.byref(nfb)), "gt_surrogate_infer")
+        return out, nfb.value

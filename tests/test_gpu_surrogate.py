@@ -1,0 +1,121 @@
+"""Surrogate network on the GPU: gradients and outputs against the FP64 CPU reference
+(oracle/mlp.py, same BF16 rounding points), training on integrator-traced rays, and
+gated inference with integrator fallback."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp
+from paper_2310_15183_gb300 import workloads as W
+
+from .parity import great_circle, to_numpy
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2310_15183_gb300 import build, geotrace
+    build.build()
+    return geotrace
+
+
+@pytest.fixture(scope="module")
+def tracer(g):
+    t = g.Tracer(0)
+    yield t
+    t.close()
+
+
+def _inputs(n, seed):
+    al, be, sp, q, th = W.surrogate_samples(n, seed=seed)
+    dev = [torch.tensor(x, dtype=torch.float64, device="cuda") for x in (al, be, sp, q, th)]
+    return (al, be, sp, q, th), dev
+
+
+def _fake_labels(n, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    st = rng.integers(0, 3, n).astype(np.uint8)
+    th, ph = rng.uniform(0.05, 3.1, n), rng.uniform(-3.1, 3.1, n)
+    dev = [torch.tensor(st, device="cuda"), torch.tensor(th, device="cuda"),
+           torch.tensor(ph, device="cuda")]
+    return (st, th, ph), dev
+
+
+def test_gradients_match_cpu_reference(g, tracer):
+    s = g.Surrogate(0, seed=11)
+    try:
+        n = 700
+        host, dev = _inputs(n, 5)
+        lab_h, lab_d = _fake_labels(n, 6)
+        grads, loss = s.grad(tracer, dev, lab_d, 10.0)
+        p = s.get_params().astype(np.float64)
+        X0 = mlp.features(*host)
+        y, d = mlp.labels(*lab_h)
+        ref_loss, ref_g, _ = mlp.loss_and_grad(p, X0, y, d, 10.0, bf=True)
+        assert abs(loss - ref_loss) < 1e-3 * abs(ref_loss), (loss, ref_loss)
+        ws, bs = mlp.split(grads.astype(np.float64))
+        rws, rbs = mlp.split(ref_g)
+        for l in range(5):
+            for a, b in ((ws[l], rws[l]), (bs[l], rbs[l])):
+                err = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+                assert err < 2e-2, (l, err)
+    finally:
+        s.close()
+
+
+def test_forward_matches_cpu_reference(g, tracer):
+    s = g.Surrogate(0, seed=12)
+    try:
+        n = 1000
+        host, dev = _inputs(n, 7)
+        out = s.eval(tracer, dev).cpu().numpy().astype(np.float64)
+        p = s.get_params().astype(np.float64)
+        _, Zs = mlp.forward(p, mlp.features(*host), bf=True)
+        ref = Zs[4][:, :4]
+        assert np.max(np.abs(out - ref)) < 2e-2 * np.max(np.abs(ref)) + 1e-3
+    finally:
+        s.close()
+
+
+def test_train_on_traced_rays_and_gated_inference(g, tracer, oracle):
+    """Label 2^15 rays with the integrator (FP32-mixed), train, and check that the gated
+    surrogate image of a Kerr camera agrees with the FP64 integrator on its confident
+    pixels while the integrator covers the rest."""
+    n = 1 << 15
+    M, r0 = 0.5, 15.0
+    host, dev = _inputs(n, 15183)
+    lab = tracer.trace_rays(*dev, M, r0, 500000, 1.5e-4, g.MODE_FP32_MIXED)
+    torch.cuda.synchronize()
+    labels = [lab["status"], lab["th"], lab["ph"]]
+    st = lab["status"].cpu().numpy()
+    assert set(np.unique(st)) <= {0, 1, 2}
+    s = g.Surrogate(0, seed=3)
+    try:
+        losses = s.train(tracer, dev, labels, epochs=30, batch=1024, lr=2e-3, dir_weight=10.0)
+        assert np.all(np.isfinite(losses)) and losses[-1] < 0.25 * losses[0], losses
+        cam = W.Camera(M=M, S=0.9 * M * M, Q=0.0, r0=r0, theta0=80 * W.DEG, fov_deg=75.0,
+                       res_x=48, res_y=48)
+        tracer.set_spacetime(cam.M, cam.S, cam.Q)
+        tracer.set_camera(cam.r0, cam.theta0, cam.fov_deg, cam.res_x, cam.res_y)
+        tracer.set_options()
+        out, nfb = s.infer(tracer, tau=2.0, band=0.05, n_steps=500000, step_precision=1.5e-4)
+        got = to_numpy(out)
+        ref = to_numpy(tracer.trace(500000, 1.5e-4, g.MODE_FP64))
+        assert 0 < nfb < cam.n_rays
+        net = got["nsteps"] == 0
+        assert net.sum() > cam.n_rays // 2
+        agree = np.mean((got["status"][net] == 0) == (ref["status"][net] == 0))
+        assert agree >= 0.97, agree
+        fb = ~net
+        assert np.array_equal(got["status"][fb], to_numpy(
+            tracer.trace(500000, 1.5e-4, g.MODE_FP32_MIXED))["status"][fb])
+        esc = net & (got["status"] == 0) & (ref["status"] == 0)
+        ang = great_circle(got["th"][esc], got["ph"][esc], ref["th"][esc], ref["ph"][esc])
+        assert np.median(ang) < 0.05, np.median(ang)
+    finally:
+        s.close()

@@ -231,6 +231,33 @@ int gt_surrogate_infer(gt_ctx *ctx, gt_surrogate *s, float tau, double band, int
                        double step_precision, int mode, double *t, double *r, double *theta,
                        double *phi, uint8_t *status, uint32_t *nsteps, int64_t *n_fallback);
 
+/* Largest batch gt_trace_batch_noalloc accepts. */
+#define GT_NOALLOC_MAX_CAMS 64
+
+/* gt_trace_batch for callers that cannot allocate device memory -- for example code
+ * inside a host framework that owns the whole device-memory budget through its own
+ * pool, or latency-critical loops where cudaMalloc's implicit device synchronisation
+ * is not acceptable.  The paper has no counterpart.
+ *
+ * No context is needed and nothing is allocated: the queue counter and the camera
+ * descriptors live in one static device array of the library (about 18 KB for
+ * GT_NOALLOC_MAX_CAMS cameras), which every device that loads the library holds until
+ * the process exits.  The caller still owns and passes the device output arrays
+ * (layout as gt_trace_batch; default launch options, no watchdog).  In FP32-mixed
+ * mode the FP64 zone steps run inline in the FP32 kernel (H = 0 re-projection every
+ * 64 steps), because the park lists gt_trace_batch uses would need allocated memory;
+ * FP64 results are identical to gt_trace_batch's.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress, with the device current); make that first
+ * call before any stream capture.  The call uploads the descriptors, synchronises
+ * `cuda_stream` to check them, clears the queue counter and launches asynchronously.
+ * All calls share the array and it keeps the last call's contents: calls whose work
+ * overlaps on the GPU (other streams, other host threads) race and must not be issued.
+ * Errors: GT_ERR_INVALID_ARG (including n_cams > GT_NOALLOC_MAX_CAMS, or a camera
+ * inside the ergoregion), GT_ERR_UNSUPPORTED (not compute capability 10.3), GT_ERR_CUDA. */
+int gt_trace_batch_noalloc(int device, void *cuda_stream, const gt_camera_desc *cams, int n_cams,
+                           int64_t n_steps, double step_precision, int mode, double *t, double *r,
+                           double *theta, double *phi, uint8_t *status, uint32_t *nsteps);
+
 /* Autotuner: time gt_trace_range over `trial_rays` central pixels of the configured
  * camera for `trial_steps` steps with every candidate launch shape (block size in
  * {64, 128, 192, 256} x resident blocks per SM in {1, 2, 3, 4, 6, 8}, within the

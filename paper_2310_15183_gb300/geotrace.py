@@ -26,7 +26,7 @@ FLAG_COMPAT_WEIGHTS, FLAG_COMPAT_CAMERA, FLAG_ONE_SHOT, FLAG_GRAPH = 1, 2, 4, 8
 # every symbol include/geotrace.h declares
 EXPORTS = ("gt_create", "gt_destroy", "gt_set_stream", "gt_set_spacetime", "gt_set_camera",
            "gt_set_options", "gt_trace", "gt_trace_range", "gt_trace_host", "gt_trace_batch", "gt_sync",
-           "gt_device_sm_count", "gt_measure_fma_peak", "gt_gemm_bf16",
+           "gt_device_sm_count", "gt_measure_fma_peak", "gt_gemm_bf16", "gt_trace_batch_noalloc",
            "gt_trace_rays", "gt_autotune", "gt_surrogate_num_params", "gt_surrogate_create",
            "gt_surrogate_destroy", "gt_surrogate_get_params", "gt_surrogate_set_params",
            "gt_surrogate_eval", "gt_surrogate_grad", "gt_surrogate_train", "gt_surrogate_infer",
@@ -92,6 +92,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.gt_measure_fma_peak.argtypes = [i, i, i, ctypes.POINTER(d)]
     lib.gt_gemm_bf16.argtypes = [i, vp, i, i, i, vp, i64, i64, vp, i64, i64, vp, i, vp, i64,
                                  i, i, i]
+    lib.gt_trace_batch_noalloc.argtypes = [i, vp, ctypes.POINTER(CameraDesc), i, i64, d, i] + out6
     lib.gt_autotune.argtypes = [vp, i, i64, i64, d, ctypes.c_char_p, ctypes.POINTER(i),
                                 ctypes.POINTER(i), ctypes.POINTER(d)]
     lib.gt_trace_rays.argtypes = [vp, i64] + [vp] * 5 + [d, d, i64, d, i] + out6

@@ -33,17 +33,45 @@ namespace gt {
 
 enum : int { KIND_KERR = 0, KIND_MN = 1 };
 
-// Derived constants of one spacetime (computed on the device by the setup kernel).
-struct SpacetimeC {
+// Derived constants of one spacetime (computed on the device by the setup kernel),
+// in the working precision T of the field evaluation.
+template <class T>
+struct SpacetimeT {
     int kind;
-    double M, a, a2;           // Kerr: a = S/M
-    double r_plus;             // outer horizon (Kerr M + sqrt(M^2 - a^2); MN M + k)
-    double k, ik, alpha, beta; // Manko-Novikov
-    double two_beta, three_beta2;
-    double c_g;                // (1 - alpha^2)^2 / k^2
-    double w_inf;              // 4 k alpha / (1 - alpha^2)
-    double k2, two_k;
+    T M, a, a2;           // Kerr: a = S/M
+    T r_plus;             // outer horizon (Kerr M + sqrt(M^2 - a^2); MN M + k)
+    T k, ik, alpha, beta; // Manko-Novikov
+    T two_beta, three_beta2;
+    T c_g;                // (1 - alpha^2)^2 / k^2
+    T w_inf;              // 4 k alpha / (1 - alpha^2)
+    T k2, inv_k2, two_k;
 };
+using SpacetimeC = SpacetimeT<double>;
+using SpacetimeF = SpacetimeT<float>;
+
+// Rounded copy for the FP32 path (done once per ray, not per field evaluation).
+template <class T>
+GT_HD SpacetimeF to_float(const SpacetimeT<T> &c)
+{
+    SpacetimeF f;
+    f.kind = c.kind;
+    f.M = (float)c.M;
+    f.a = (float)c.a;
+    f.a2 = (float)c.a2;
+    f.r_plus = (float)c.r_plus;
+    f.k = (float)c.k;
+    f.ik = (float)c.ik;
+    f.alpha = (float)c.alpha;
+    f.beta = (float)c.beta;
+    f.two_beta = (float)c.two_beta;
+    f.three_beta2 = (float)c.three_beta2;
+    f.c_g = (float)c.c_g;
+    f.w_inf = (float)c.w_inf;
+    f.k2 = (float)c.k2;
+    f.inv_k2 = (float)c.inv_k2;
+    f.two_k = (float)c.two_k;
+    return f;
+}
 
 template <class T>
 struct Rates {
@@ -165,7 +193,7 @@ GT_HD void mkvar(V1<T> &o, T v, T, T) { o = {v}; }
 
 // ------------------------------------------------------------------ Kerr
 template <class T>
-GT_HD void kerr_rates(const SpacetimeC &c, T r, T th, T pr, T pth, T pt,
+GT_HD void kerr_rates(const SpacetimeT<T> &c, T r, T th, T pr, T pth, T pt,
                                            T pph, Rates<T> &o)
 {
     T s, cs;
@@ -222,7 +250,7 @@ struct MNPot {
 
 // N = D3<T> (values and r, theta derivatives) or V1<T> (values only).
 template <class T, class N>
-GT_HD void mn_potentials(const SpacetimeC &c, T r, T th, MNPot<N> &P)
+GT_HD void mn_potentials(const SpacetimeT<T> &c, T r, T th, MNPot<N> &P)
 {
     T s, cs;
     sincos_t(th, &s, &cs);
@@ -263,14 +291,14 @@ GT_HD void mn_potentials(const SpacetimeC &c, T r, T th, MNPot<N> &P)
     const N iA = drcp(A);
     const N iB = drcp(B);
     P.invf = ie2psi * B * iA;
-    P.F = e2psi * A * iB * drcp(x2m1 * s2) * T(1.0 / c.k2);
+    P.F = e2psi * A * iB * drcp(x2m1 * s2) * T(c.inv_k2);
     P.om = ie2psi * C * iA * T(c.two_k) - T(c.w_inf);
     P.G = dexp(psi2 - g2) * iB * T(c.c_g);
     P.Delta = x2m1 * T(c.k2);
 }
 
 template <class T>
-GT_HD void mn_rates(const SpacetimeC &c, T r, T th, T pr, T pth, T pt, T pph,
+GT_HD void mn_rates(const SpacetimeT<T> &c, T r, T th, T pr, T pth, T pt, T pph,
                                          Rates<T> &o)
 {
     MNPot<D3<T>> P;
@@ -299,7 +327,7 @@ __device__ __forceinline__ void mn_upper(const SpacetimeC &c, double r, double t
 }
 
 template <int KIND, class T>
-GT_HD void rates(const SpacetimeC &c, T r, T th, T pr, T pth, T pt, T pph,
+GT_HD void rates(const SpacetimeT<T> &c, T r, T th, T pr, T pth, T pt, T pph,
                                       Rates<T> &o)
 {
     if (KIND == KIND_KERR)

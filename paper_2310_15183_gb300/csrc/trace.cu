@@ -59,6 +59,7 @@ __device__ void setup_desc(CamDesc &d, int flags, double r_switch)
         st.c_g = (1.0 - al * al) * (1.0 - al * al) / (k * k);
         st.w_inf = 4.0 * k * al / (1.0 - al * al);
         st.k2 = k * k;
+        st.inv_k2 = 1.0 / (k * k);
         st.two_k = 2.0 * k;
         st.r_plus = d.M + k;
     } else {
@@ -254,7 +255,7 @@ __device__ __forceinline__ void mixed_to64(const RayMixed &m, Ray64 &x)
 }
 
 template <int KIND>
-__device__ __forceinline__ void rates_f32(const SpacetimeC &st, float r, float th, float pr,
+__device__ __forceinline__ void rates_f32(const SpacetimeF &st, float r, float th, float pr,
                                           float pth, float pt, float pph, Rates<float> &o)
 {
     if (KIND == 2) {
@@ -269,7 +270,7 @@ __device__ __forceinline__ void rates_f32(const SpacetimeC &st, float r, float t
 
 // One FP32 RK4 step on the compensated state; returns h (as float).
 template <int KIND>
-__device__ __forceinline__ float rk4_step32(const SpacetimeC &st, RayMixed &m, float sp, float w6)
+__device__ __forceinline__ float rk4_step32(const SpacetimeF &st, RayMixed &m, float sp, float w6)
 {
     Rates<float> k1, k2, k3, k4;
     const float r = m.r.hi, th = m.th.hi, pr = m.pr.hi, pth = m.pth.hi;
@@ -364,6 +365,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A, int one_shot)
     Ray64 x;
     RayMixed m;
     SpacetimeC st = cams[0].st;
+    SpacetimeF stf = to_float(st);
     double r_esc = cams[0].r_escape;
     double r_sw = cams[0].r_switch;
     const float spf = (float)A.sp, w6f = (float)A.w6;
@@ -376,6 +378,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A, int one_shot)
         st = cams[c].st;
         r_esc = cams[c].r_escape;
         r_sw = cams[c].r_switch;
+        if (MODE == 1 || MODE == 2) stf = to_float(st);
         if (MODE == 2) {
             r_esc_f = f2_from(r_esc);
             r_sw_f = (float)r_sw;
@@ -395,6 +398,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A, int one_shot)
         st = d.st;
         r_esc = d.r_escape;
         r_sw = d.r_switch;
+        if (MODE == 1 || MODE == 2) stf = to_float(st);
         if (MODE == 2) {
             r_esc_f = f2_from(r_esc);
             r_sw_f = (float)r_sw;
@@ -543,7 +547,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A, int one_shot)
                 if (ok) mixed_from64(y, m);
             } else {
                 RayMixed keep = m;
-                h = (double)rk4_step32<KIND>(st, m, spf, w6f);
+                h = (double)rk4_step32<KIND>(stf, m, spf, w6f);
                 ok = isfinite(h) && isfinite(m.t.hi) && isfinite(m.r.hi) && isfinite(m.th.hi) &&
                      isfinite(m.ph.hi) && isfinite(m.pr.hi) && isfinite(m.pth.hi);
                 if (!ok) m = keep;
@@ -565,7 +569,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A, int one_shot)
             }
         } else { // MODE 2: FP32 steps only, exit tests in FP32
             RayMixed keep = m;
-            const float h = rk4_step32<KIND>(st, m, spf, w6f);
+            const float h = rk4_step32<KIND>(stf, m, spf, w6f);
             ++n;
             const bool ok = isfinite(h) && isfinite(m.t.hi) && isfinite(m.r.hi) &&
                             isfinite(m.th.hi) && isfinite(m.ph.hi) && isfinite(m.pr.hi) &&

@@ -43,21 +43,22 @@ static void print_counts(const char *name, const Counts &c, bool last)
 
 int main()
 {
-    gt::SpacetimeC st = {};
+    gt::SpacetimeT<CN> st = {};
     st.M = 0.5;
     st.a = 0.48;
-    st.a2 = st.a * st.a;
+    st.a2 = 0.48 * 0.48;
     st.k = 0.14;
-    st.ik = 1.0 / st.k;
+    st.ik = 1.0 / 0.14;
     st.alpha = -0.75;
     st.beta = 91.1;
-    st.two_beta = 2 * st.beta;
-    st.three_beta2 = 3 * st.beta * st.beta;
+    st.two_beta = 2 * 91.1;
+    st.three_beta2 = 3 * 91.1 * 91.1;
     st.c_g = 1.0;
     st.w_inf = 0.1;
-    st.k2 = st.k * st.k;
-    st.two_k = 2 * st.k;
-    st.r_plus = st.M + st.k;
+    st.k2 = 0.14 * 0.14;
+    st.inv_k2 = 1.0 / (0.14 * 0.14);
+    st.two_k = 2 * 0.14;
+    st.r_plus = 0.5 + 0.14;
     gt::Rates<CN> o;
     g_c = Counts();
     gt::kerr_rates<CN>(st, CN(5.0), CN(1.1), CN(0.2), CN(0.3), CN(0.9), CN(-2.0), o);

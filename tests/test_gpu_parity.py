@@ -275,3 +275,50 @@ def test_mixed_full_size_sampled(tracer, oracle):
     assert rep["agree"] == 1.0 and rep["max_angle"] < 1e-4, rep
     for k in ("t", "r"):
         assert np.max(np.abs(sub[k] - ref[k]) / np.abs(ref[k])) < 1e-4
+
+
+# ----------------------------------------------------------------- autotuner and graphs
+def test_autotuner_picks_valid_shape_caches_it_and_keeps_bits(g, tracer, tmp_path):
+    cam = W.sub_camera(MN, 96, 64)
+    base = run_gpu(tracer, cam, 2500, 1.5e-4, mode=0)
+    cache = str(tmp_path / "tune.txt")
+    b, k, v = tracer.autotune(0, trial_rays=4096, trial_steps=200, cache_path=cache)
+    assert b in (64, 128, 192, 256) and 1 <= k <= 8 and v > 0
+    assert open(cache).read().count("|") == 1
+    b2, k2, v2 = tracer.autotune(0, trial_rays=4096, trial_steps=200, cache_path=cache)
+    assert (b2, k2) == (b, k)
+    out = to_numpy(tracer.trace(2500, 1.5e-4, 0))  # tuned shape kept in the context
+    torch.cuda.synchronize()
+    for key in ("t", "r", "th", "ph", "status", "nsteps"):
+        assert np.array_equal(out[key], base[key]), key
+
+
+def test_graph_launch_replays_the_batch(g, tracer, oracle):
+    """GT_FLAG_GRAPH: the batched trace as one persistent launch replayed from a cached
+    CUDA graph -- FP64 bitwise equal to the direct launch, twice in a row; FP32-mixed
+    (FP64 zone inline) within the mixed-precision criteria."""
+    cams = [W.Camera(0.5, 0.1, 0.0, 12.0, 0.7, 75.0, 13, 9),
+            W.Camera(0.5, 0.2475, 0.0, 20.0, 1.5, 60.0, 5, 17),
+            W.Camera(0.5, 0.24, 0.0, 15.0, 80 * W.DEG, 30.0, 12, 10)]
+    tracer.set_options()
+    direct = to_numpy(tracer.trace_batch(cams, 300000, 1.5e-4, 0))
+    tracer.set_options(flags=g.FLAG_GRAPH)
+    out = tracer.alloc_outputs(sum(c.n_rays for c in cams))
+    for _ in range(2):
+        for v in out.values():
+            v.zero_()
+        got = to_numpy(tracer.trace_batch(cams, 300000, 1.5e-4, 0, out=out))
+        torch.cuda.synchronize()
+        for key in ("t", "r", "th", "ph", "status", "nsteps"):
+            assert np.array_equal(got[key], direct[key]), key
+    mixed = to_numpy(tracer.trace_batch(cams, 300000, 1.5e-4, 1))
+    torch.cuda.synchronize()
+    tracer.set_options()
+    off = 0
+    for c in cams:
+        sl = slice(off, off + c.n_rays)
+        band = neighbour_band(direct["status"][sl], c.res_x, c.res_y)
+        rep = mixed_report({k: v[sl] for k, v in mixed.items()},
+                           {k: v[sl] for k, v in direct.items()}, exclude=band)
+        assert rep["agree"] >= 0.999 and rep["max_angle_escaped"] <= 1e-3, rep
+        off += c.n_rays

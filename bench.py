@@ -27,6 +27,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+from paper_2310_15183_gb300 import sharding  # noqa: E402
 from paper_2310_15183_gb300 import workloads as W  # noqa: E402
 
 METRIC = "RK4 geodesic steps/s & rays/s on GB300: FP64 plain vs FP32-mixed vs surrogate"
@@ -161,6 +162,172 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ extra legs
+def _timed(torch, stream, fn):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    return r, e0.elapsed_time(e1) / 1e3
+
+
+def _steps(out):
+    import numpy as np
+    return float(out["nsteps"].cpu().numpy().view(np.uint32).astype(np.float64).sum())
+
+
+def leg_batch(tr, geotrace, args, torch):
+    """64 Kerr cameras of uneven size (sides / batch_scale), 500,000-step cap, FP32-mixed:
+    autotuned launch shape, one persistent launch replayed from a CUDA graph (FP64 zone
+    inline) and the round-based launch for comparison."""
+    import dataclasses
+    cams = [dataclasses.replace(c, res_x=max(1, c.res_x // args.batch_scale),
+                                res_y=max(1, c.res_y // args.batch_scale))
+            for c in W.batch_cameras()]
+    n = sum(c.n_rays for c in cams)
+    rep = cams[0]
+    tr.set_spacetime(rep.M, rep.S, rep.Q)
+    tr.set_camera(rep.r0, rep.theta0, rep.fov_deg, 256, 256)
+    tr.set_options()
+    b, k, v = tr.autotune(geotrace.MODE_FP32_MIXED, trial_rays=1 << 16, trial_steps=300,
+                          cache_path=os.path.join(ROOT, "paper_2310_15183_gb300", "_build", "autotune.txt"))
+    res = {"cameras": len(cams), "rays": n, "n_steps": 500000,
+           "sides": [min(c.res_x for c in cams), max(c.res_x for c in cams)],
+           "scale": f"camera sides divided by {args.batch_scale}",
+           "autotuned": {"block_size": b, "blocks_per_sm": k, "trial_steps_per_s": v}}
+    out = tr.alloc_outputs(n)
+    for label, flags in (("graph", geotrace.FLAG_GRAPH), ("rounds", 0)):
+        tr.set_options(block_size=b, blocks_per_sm=k, flags=flags)
+        tr.trace_batch(cams, 500000, 1.5e-4, geotrace.MODE_FP32_MIXED, out=out)  # warm-up/capture
+        _, t = _timed(torch, tr.stream,
+                      lambda: tr.trace_batch(cams, 500000, 1.5e-4, geotrace.MODE_FP32_MIXED, out=out))
+        st = _steps(out)
+        res[label] = {"seconds": t, "steps_per_s": st / t, "rays_per_s": n / t}
+    tr.set_options()
+    return res
+
+
+def leg_surrogate(tr, geotrace, args, torch):
+    """Surrogate: label sg_samples rays with the integrator (FP32-mixed, 500,000-step cap)
+    over the batch ranges at r0 = 30M, train, then image a sg_res^2 Kerr camera (a = 0.9M,
+    80 deg) with gating + integrator fallback; integrator-only time from a pixel subsample;
+    accuracy against the FP64 integrator on a 64x64 pixel subsample."""
+    import numpy as np
+    M, r0, sp, cap = 0.5, 15.0, 1.5e-4, 500000
+    host = W.surrogate_samples(args.sg_samples, seed=15183, M=M, r0=r0)
+    dev = [torch.tensor(x, dtype=torch.float64, device="cuda") for x in host]
+    lab, t_label = _timed(torch, tr.stream,
+                          lambda: tr.trace_rays(*dev, M, r0, cap, sp, geotrace.MODE_FP32_MIXED))
+    labels = [lab["status"], lab["th"], lab["ph"]]
+    sg = geotrace.Surrogate(0, r0=r0, seed=7)
+    t0 = time.perf_counter()
+    losses = sg.train(tr, dev, labels, epochs=args.sg_epochs, batch=4096, lr=2e-3,
+                      dir_weight=10.0)
+    t_train = time.perf_counter() - t0
+    cam = W.Camera(M=M, S=0.9 * M * M, Q=0.0, r0=r0, theta0=80 * W.DEG, fov_deg=75.0,
+                   res_x=args.sg_res, res_y=args.sg_res)
+    tr.set_spacetime(cam.M, cam.S, cam.Q)
+    tr.set_camera(cam.r0, cam.theta0, cam.fov_deg, cam.res_x, cam.res_y)
+    tr.set_options()
+    res = {"train_rays": args.sg_samples, "label_seconds": t_label,
+           "label_steps_per_s": _steps(lab) / t_label, "train_seconds": t_train,
+           "epochs": args.sg_epochs, "loss_first_last": [float(losses[0]), float(losses[-1])],
+           "image": [cam.res_x, cam.res_y]}
+    step = max(1, cam.res_x // 64)
+    jj, ii = np.meshgrid(np.arange(step // 2, cam.res_y, step), np.arange(step // 2, cam.res_x, step),
+                         indexing="ij")
+    judge_pix = (jj * cam.res_x + ii).ravel().astype(np.int64)
+    judge = tr.trace_pixels(torch.tensor(judge_pix, device="cuda"), cap, sp, geotrace.MODE_FP64)
+    torch.cuda.synchronize()
+    jd = {k: (v.cpu().numpy().view(np.uint32) if k == "nsteps" else v.cpu().numpy())
+          for k, v in judge.items()}
+    sub_step = max(1, cam.res_x // 256)
+    jj, ii = np.meshgrid(np.arange(sub_step // 2, cam.res_y, sub_step),
+                         np.arange(sub_step // 2, cam.res_x, sub_step), indexing="ij")
+    sub_pix = torch.tensor((jj * cam.res_x + ii).ravel().astype(np.int64), device="cuda")
+    sub, t_sub = _timed(torch, tr.stream,
+                        lambda: tr.trace_pixels(sub_pix, cap, sp, geotrace.MODE_FP32_MIXED))
+    integ_full_s = t_sub * cam.n_rays / sub_pix.numel()
+    mix = tr.trace_pixels(torch.tensor(judge_pix, device="cuda"), cap, sp, geotrace.MODE_FP32_MIXED)
+    torch.cuda.synchronize()
+    md = {k: v.cpu().numpy() for k, v in mix.items()}
+
+    def angle(a_th, a_ph, b_th, b_ph):
+        h = (np.sin((b_th - a_th) / 2) ** 2 +
+             np.sin(a_th) * np.sin(b_th) * np.sin((b_ph - a_ph) / 2) ** 2)
+        return 2 * np.arcsin(np.sqrt(np.clip(h, 0, 1)))
+
+    def accuracy(got):
+        same = (got["status"] == 0) == (jd["status"] == 0)
+        both = (got["status"] == 0) & (jd["status"] == 0)
+        ang = angle(got["th"][both], got["ph"][both], jd["th"][both], jd["ph"][both])
+        return {"classification_agreement": float(same.mean()),
+                "angle_err_max": float(ang.max()) if ang.size else 0.0,
+                "angle_err_p99": float(np.percentile(ang, 99)) if ang.size else 0.0,
+                "angle_err_median": float(np.median(ang)) if ang.size else 0.0}
+
+    res["fp32_mixed_vs_fp64"] = accuracy(md)
+    for tau, band in ((2.0, 0.02), (4.0, 0.05)):
+        out = tr.alloc_outputs(cam.n_rays)
+        (out, nfb), t_inf = _timed(torch, tr.stream,
+                                   lambda: sg.infer(tr, tau, band, cap, sp,
+                                                    geotrace.MODE_FP32_MIXED, out=out))
+        got = {k: out[k][torch.tensor(judge_pix, device="cuda")].cpu().numpy()
+               for k in ("status", "th", "ph")}
+        res[f"tau{tau}_band{band}"] = {
+            "seconds": t_inf, "fallback_pixels": nfb, "fallback_frac": nfb / cam.n_rays,
+            "speedup_vs_integrator_only": integ_full_s / t_inf, **accuracy(got)}
+    res["integrator_only_seconds_extrapolated"] = integ_full_s
+    res["integrator_subsample"] = f"{sub_pix.numel()} pixels (every {sub_step}th in x and y)"
+    res["judge"] = f"FP64 integrator on {judge_pix.size} pixels (every {step}th in x and y)"
+    sg.close()
+    return res
+
+
+def leg_sweep(tr, geotrace, args, torch):
+    """Inclination sweep at a = 0.9M, 4096^2, step_precision 2e-5, 200,000 steps: frames
+    k = 0, 21, 42, 63 of 64 (theta0 = 5 + 85 k/63 deg) on a 256x256 pixel subsample
+    (pixels 16m+8), FP64 plain vs FP32-mixed; the FP64 CPU oracle judges a 16x16 subsample
+    (pixels 256m+128) of each frame."""
+    import numpy as np
+
+    import oracle
+    res, frames = {}, (0, 21, 42, 63)
+    jj, ii = np.meshgrid(np.arange(8, 4096, 16), np.arange(8, 4096, 16), indexing="ij")
+    pix = (jj * 4096 + ii).ravel().astype(np.int64)
+    dpix = torch.tensor(pix, device="cuda")
+    oj, oi = np.meshgrid(np.arange(128, 4096, 256), np.arange(128, 4096, 256), indexing="ij")
+    opix = (oj * 4096 + oi).ravel().astype(np.int64)
+    sel = np.searchsorted(pix, opix)
+    for k in frames:
+        th0 = (5 + 85 * k / 63) * W.DEG
+        tr.set_spacetime(0.5, 0.9 * 0.25, 0.0)
+        tr.set_camera(15.0, th0, 75.0, 4096, 4096)
+        tr.set_options()
+        f = {}
+        for name, mode in (("fp64", geotrace.MODE_FP64), ("fp32_mixed", geotrace.MODE_FP32_MIXED)):
+            out, t = _timed(torch, tr.stream,
+                            lambda: tr.trace_pixels(dpix, 200000, 2e-5, mode))
+            o = {kk: (v.cpu().numpy().view(np.uint32) if kk == "nsteps" else v.cpu().numpy())
+                 for kk, v in out.items()}
+            f[name] = {"seconds": t, "steps_per_s": float(o["nsteps"].astype(float).sum()) / t,
+                       "out": o}
+        ref = oracle.trace_image(0.5, 0.225, 0.0, 15.0, th0, 75.0, 4096, 4096, 200000, 2e-5,
+                                 pixels=opix)
+        for name in ("fp64", "fp32_mixed"):
+            o = f[name].pop("out")
+            err = max(float(np.max(np.abs(o[kk][sel] - ref[kk]) / np.maximum(1, np.abs(ref[kk]))))
+                      for kk in ("t", "r", "th", "ph"))
+            f[name]["max_rel_err_vs_oracle"] = err
+            f[name]["status_equal"] = bool(np.array_equal(o["status"][sel], ref["status"]))
+        res[f"frame{k}"] = f
+    res["subsample"] = "256x256 pixels (16m+8) of 4096x4096; oracle on 16x16 (256m+128)"
+    return res
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -173,6 +340,12 @@ def main():
     ap.add_argument("--fp64-rows", type=int, default=64,
                     help="image rows traced by the FP64 plain leg (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--legs", default="", help="extra legs: batch,surrogate,sweep (comma list)")
+    ap.add_argument("--sg-samples", type=int, default=1 << 22)
+    ap.add_argument("--sg-epochs", type=int, default=12)
+    ap.add_argument("--sg-res", type=int, default=4096)
+    ap.add_argument("--batch-scale", type=int, default=8,
+                    help="batch leg: camera sides divided by this factor")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -204,7 +377,7 @@ def main():
 
     wl = W.WORKLOADS[args.workload]
     cam = wl.camera
-    th0 = cam.theta0 - rank * W.DEG if world > 1 else cam.theta0
+    th0 = sharding.sweep_camera(cam, rank, world).theta0
     mode = geotrace.MODE_FP32_MIXED if args.mode == "mixed" else geotrace.MODE_FP64
     tr = geotrace.Tracer(local)
     stream = tr.stream
@@ -239,11 +412,7 @@ def main():
     status = out["status"].cpu().numpy()
     steps_per_pass = float(nsteps.sum())
     if dist is not None:
-        tt = torch.tensor([t_dev, steps_per_pass], dtype=torch.float64, device="cuda")
-        tmax = tt.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
-        t_job, steps_job = float(tmax[0]), float(tt[1])
+        t_job, steps_job = sharding.reduce_timing(dist, t_dev, steps_per_pass, device="cuda")
     else:
         t_job, steps_job = t_dev, steps_per_pass
     value = args.steps * steps_job / t_job
@@ -326,6 +495,20 @@ def main():
         cpu = {"value": r["steps_per_s"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
                "sample": r["sample"], "rays_per_s": r["rays_per_s"], "seconds": r["seconds"]}
 
+    legs = {}
+    for leg in [x for x in args.legs.split(",") if x]:
+        t0 = time.perf_counter()
+        if leg == "batch":
+            legs["batch"] = leg_batch(tr, geotrace, args, torch)
+        elif leg == "surrogate":
+            legs["surrogate"] = leg_surrogate(tr, geotrace, args, torch)
+        elif leg == "sweep":
+            legs["sweep"] = leg_sweep(tr, geotrace, args, torch)
+        else:
+            raise SystemExit(f"unknown leg {leg}")
+        legs[leg]["leg_wall_s"] = time.perf_counter() - t0
+        log(f"leg {leg}: {legs[leg]}")
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -346,6 +529,8 @@ def main():
             "roofline": roofline, "modes": modes, "e2e": e2e, "cpu_baseline": cpu,
             "clocks": clocks, "gpu_launches": args.steps,
         }
+        if legs:
+            line["legs"] = legs
         print(json.dumps(line), flush=True)
     tr.close()
     if dist is not None:

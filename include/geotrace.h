@@ -138,6 +138,14 @@ int gt_trace_range(gt_ctx *ctx, int64_t first, int64_t count, int64_t n_steps,
                    double step_precision, int mode, double *t, double *r, double *theta,
                    double *phi, uint8_t *status, uint32_t *nsteps);
 
+/* As gt_trace for the `n` flat pixel indices in `pixels` (a DEVICE int64 array, each in
+ * [0, res_x*res_y); the caller keeps them in range -- they are not checked on the host);
+ * output element k belongs to pixels[k].  Used to subsample large images.
+ * Errors as gt_trace. */
+int gt_trace_pixels(gt_ctx *ctx, const int64_t *pixels, int64_t n, int64_t n_steps,
+                    double step_precision, int mode, double *t, double *r, double *theta,
+                    double *phi, uint8_t *status, uint32_t *nsteps);
+
 /* As gt_trace, but the outputs are HOST arrays: the library copies the results
  * back (through its own device staging buffers) and returns after they arrived. */
 int gt_trace_host(gt_ctx *ctx, int64_t n_steps, double step_precision, int mode, double *t,

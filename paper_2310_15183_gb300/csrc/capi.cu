@@ -235,7 +235,8 @@ int run_mixed_rounds(gt_ctx *c, gt::TraceArgs &a, int kind_hint, const gt_option
 int run_trace(gt_ctx *c, const CamDesc *d_cams, int n_cams, int kind_hint, int64_t first,
               int64_t n_rays, int64_t n_steps, double sp, int mode, double *t, double *r,
               double *th, double *ph, uint8_t *status, uint32_t *nsteps,
-              const int64_t *fresh_ids = nullptr, const gt::RayParams *d_rays = nullptr)
+              const int64_t *fresh_ids = nullptr, const gt::RayParams *d_rays = nullptr,
+              bool compact_out = false)
 {
     const gt_options e = effective(c->opts);
     if (n_rays == 0) return GT_OK;
@@ -247,6 +248,7 @@ int run_trace(gt_ctx *c, const CamDesc *d_cams, int n_cams, int kind_hint, int64
     a.n_fresh = n_rays;
     a.first = first;
     a.fresh_ids = fresh_ids;
+    a.compact_out = compact_out ? 1 : 0;
     a.rays = d_rays;
     a.n_steps = n_steps;
     a.sp = sp;
@@ -487,6 +489,26 @@ int gt_trace_range(gt_ctx *c, int64_t first, int64_t count, int64_t n_steps, dou
     const int kind = (c->Q != 0.0) ? gt::KIND_MN : gt::KIND_KERR;
     return run_trace(c, c->d_cam, 1, kind, first, count, n_steps, sp, mode, t, r, th, ph, status,
                      nsteps);
+}
+
+int gt_trace_pixels(gt_ctx *c, const int64_t *pixels, int64_t n, int64_t n_steps, double sp,
+                    int mode, double *t, double *r, double *th, double *ph, uint8_t *status,
+                    uint32_t *nsteps)
+{
+    int rc = check_common(c, n_steps, sp, mode);
+    if (rc != GT_OK) return rc;
+    if (!c->st_set || !c->cam_set) return GT_ERR_NOT_CONFIGURED;
+    if (n < 0 || (n > 0 && !pixels)) return GT_ERR_INVALID_ARG;
+    if (!aligned8(t) || !aligned8(r) || !aligned8(th) || !aligned8(ph) || ((uintptr_t)nsteps & 3u))
+        return GT_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    if (!g.ok) return GT_ERR_CUDA;
+    rc = prepare_camera(c);
+    if (rc != GT_OK) return rc;
+    if (!c->cam_valid) return GT_ERR_INVALID_ARG;
+    const int kind = (c->Q != 0.0) ? gt::KIND_MN : gt::KIND_KERR;
+    return run_trace(c, c->d_cam, 1, kind, 0, n, n_steps, sp, mode, t, r, th, ph, status, nsteps,
+                     pixels, nullptr, true);
 }
 
 int gt_trace_host(gt_ctx *c, int64_t n_steps, double sp, int mode, double *t, double *r,

@@ -67,8 +67,8 @@ struct TraceArgs {
     int64_t n_fresh;  // fresh rays started by this launch, ids [0, n_fresh); output index
                       // k belongs to flat ray first + k
     int64_t first;    // first flat ray id (single-camera range traces)
-    const int64_t *fresh_ids; // when set, fresh work item w is ray fresh_ids[w] (and its
-                              // output index); otherwise ray w
+    const int64_t *fresh_ids; // when set, fresh work item w is ray fresh_ids[w]; otherwise ray w
+    int compact_out;          // with fresh_ids: output index w instead of fresh_ids[w]
     const ParkItem *in_items;                // input list (modes 2, 3) or null
     const unsigned long long *in_count;      // its length (device word) or null
     unsigned long long in_cap;               // capacity of the input list

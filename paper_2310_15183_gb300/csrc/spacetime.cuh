@@ -84,7 +84,10 @@ struct Rates {
 __device__ __forceinline__ void sincos_t(double x, double *s, double *c) { sincos(x, s, c); }
 __device__ __forceinline__ void sincos_t(float x, float *s, float *c) { sincosf(x, s, c); }
 __device__ __forceinline__ double exp_t(double x) { return exp(x); }
-__device__ __forceinline__ float exp_t(float x) { return expf(x); }
+__device__ __forceinline__ float exp_t(float x) { return __expf(x); } // FP32 path: fast
+// reciprocal: IEEE in FP64 (the parity path), the fast hardware approximation in FP32
+__device__ __forceinline__ double rcp_t(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rcp_t(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
@@ -132,7 +135,7 @@ GT_HD D3<T> dsq(D3<T> a)
 template <class T>
 GT_HD D3<T> drcp(D3<T> a)
 {
-    const T iv = T(1) / a.v;
+    const T iv = rcp_t(a.v);
     const T w = -iv * iv;
     return {iv, a.r * w, a.t * w};
 }
@@ -179,7 +182,7 @@ GT_HD V1<T> operator*(V1<T> a, V1<T> b) { return {a.v * b.v}; }
 template <class T>
 GT_HD V1<T> dsq(V1<T> a) { return {a.v * a.v}; }
 template <class T>
-GT_HD V1<T> drcp(V1<T> a) { return {T(1) / a.v}; }
+GT_HD V1<T> drcp(V1<T> a) { return {rcp_t(a.v)}; }
 template <class T>
 GT_HD V1<T> drsqrt(V1<T> a) { return {rsqrt_t(a.v)}; }
 template <class T>
@@ -203,7 +206,7 @@ GT_HD void kerr_rates(const SpacetimeT<T> &c, T r, T th, T pr, T pth, T pt,
     const T s2 = s * s;
     const T Sigma = fma_t(a2, cs * cs, r2);
     const T Delta = fma_t(r, r - T(2) * M, a2);
-    const T inv = T(1) / (Sigma * Delta * s2); // one division for 1/Sigma, 1/Delta, 1/sin^2
+    const T inv = rcp_t(Sigma * Delta * s2); // one reciprocal for 1/Sigma, 1/Delta, 1/sin^2
     const T iSigma = Delta * s2 * inv;
     const T iDelta = Sigma * s2 * inv;
     const T is2 = Sigma * Delta * inv;

@@ -375,10 +375,12 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A, int one_shot)
 
     auto load_camera = [&](int c) {
         cam = c;
-        st = cams[c].st;
+        // the FP32-only kernel keeps just the float constants live; the FP64 ones are
+        // reloaded for the occasional re-projection
+        if (MODE != 2) st = cams[c].st;
         r_esc = cams[c].r_escape;
         r_sw = cams[c].r_switch;
-        if (MODE == 1 || MODE == 2) stf = to_float(st);
+        if (MODE == 1 || MODE == 2) stf = to_float(cams[c].st);
         if (MODE == 2) {
             r_esc_f = f2_from(r_esc);
             r_sw_f = (float)r_sw;
@@ -395,10 +397,10 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A, int one_shot)
         d.res_x = d.res_y = 1;
         d.offset = 0;
         setup_desc(d, A.flags, A.rays->r_switch);
-        st = d.st;
+        if (MODE != 2) st = d.st;
         r_esc = d.r_escape;
         r_sw = d.r_switch;
-        if (MODE == 1 || MODE == 2) stf = to_float(st);
+        if (MODE == 1 || MODE == 2) stf = to_float(d.st);
         if (MODE == 2) {
             r_esc_f = f2_from(r_esc);
             r_sw_f = (float)r_sw;
@@ -411,12 +413,12 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A, int one_shot)
     auto start = [&](int64_t w) -> bool {
         if (w < A.n_fresh) { // a fresh ray: initial data from the camera
             const int64_t pix = A.fresh_ids ? A.fresh_ids[w] : w;
-            id = pix;
+            id = (A.fresh_ids && A.compact_out) ? w : pix;
             if (A.rays) {
                 const bool valid = load_rayparams(pix, true);
                 n = 0;
                 if (!valid || A.n_steps <= 0) {
-                    store_ray(A, pix, x.t, x.r, x.th, x.ph, valid ? GT_RAY_MAXSTEPS : GT_RAY_NONFINITE, 0);
+                    store_ray(A, id, x.t, x.r, x.th, x.ph, valid ? GT_RAY_MAXSTEPS : GT_RAY_NONFINITE, 0);
                     return false;
                 }
             } else {
@@ -424,7 +426,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A, int one_shot)
                 camera_init(cams[cam], A.first + pix - cams[cam].offset, x);
                 n = 0;
                 if (A.n_steps <= 0) {
-                    store_ray(A, pix, x.t, x.r, x.th, x.ph, GT_RAY_MAXSTEPS, 0);
+                    store_ray(A, id, x.t, x.r, x.th, x.ph, GT_RAY_MAXSTEPS, 0);
                     return false;
                 }
             }
@@ -506,7 +508,8 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A, int one_shot)
                                 const int c = A.n_cams > 1 ? find_camera(cams, A.n_cams, pix) : 0;
                                 const double r0 = A.rays ? A.rays->r0 : cams[c].r0;
                                 const double th0 = A.rays ? A.rays->theta0[pix] : cams[c].th0;
-                                store_ray(A, pix, 0.0, r0, th0, 0.0, GT_RAY_TIMEOUT, 0);
+                                store_ray(A, (A.fresh_ids && A.compact_out) ? w : pix, 0.0, r0,
+                                          th0, 0.0, GT_RAY_TIMEOUT, 0);
                             } else {
                                 const ParkItem &p = A.in_items[w - A.n_fresh];
                                 store_ray(A, p.id, p.t, p.r, p.th, p.ph, GT_RAY_TIMEOUT, p.n);
@@ -590,7 +593,23 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A, int one_shot)
                 if (parked) active = false;
             } else if (A.reproject_every > 0 && (n % (uint32_t)A.reproject_every) == 0u) {
                 mixed_to64(m, x);
-                reproject_pr(st, x);
+                SpacetimeC st64;
+                if (A.rays) {
+                    CamDesc d;
+                    d.M = A.rays->M;
+                    d.S = A.rays->spin[id] * A.rays->M;
+                    d.Q = A.rays->q[id];
+                    d.r0 = A.rays->r0;
+                    d.th0 = A.rays->theta0[id];
+                    d.fov_deg = 90.0;
+                    d.res_x = d.res_y = 1;
+                    d.offset = 0;
+                    setup_desc(d, A.flags, A.rays->r_switch);
+                    st64 = d.st;
+                } else {
+                    st64 = cams[cam].st;
+                }
+                reproject_pr(st64, x);
                 m.pr = f2_from(x.pr);
             }
             if (status >= 0) mixed_to64(m, x);

@@ -25,7 +25,7 @@ FLAG_COMPAT_WEIGHTS, FLAG_COMPAT_CAMERA, FLAG_ONE_SHOT, FLAG_GRAPH = 1, 2, 4, 8
 
 # every symbol include/geotrace.h declares
 EXPORTS = ("gt_create", "gt_destroy", "gt_set_stream", "gt_set_spacetime", "gt_set_camera",
-           "gt_set_options", "gt_trace", "gt_trace_range", "gt_trace_host", "gt_trace_batch", "gt_sync",
+           "gt_set_options", "gt_trace", "gt_trace_range", "gt_trace_pixels", "gt_trace_host", "gt_trace_batch", "gt_sync",
            "gt_device_sm_count", "gt_measure_fma_peak", "gt_gemm_bf16", "gt_trace_batch_noalloc",
            "gt_trace_rays", "gt_autotune", "gt_surrogate_num_params", "gt_surrogate_create",
            "gt_surrogate_destroy", "gt_surrogate_get_params", "gt_surrogate_set_params",
@@ -85,6 +85,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     out6 = [vp] * 6
     lib.gt_trace.argtypes = [vp, i64, d, i] + out6
     lib.gt_trace_range.argtypes = [vp, i64, i64, i64, d, i] + out6
+    lib.gt_trace_pixels.argtypes = [vp, vp, i64, i64, d, i] + out6
     lib.gt_trace_host.argtypes = [vp, i64, d, i] + out6
     lib.gt_trace_batch.argtypes = [vp, ctypes.POINTER(CameraDesc), i, i64, d, i] + out6
     lib.gt_sync.argtypes = [vp]
@@ -213,6 +214,19 @@ class Tracer:
                                      *[_ptr(out.get(k)) for k in ("t", "r", "th", "ph",
                                                                    "status", "nsteps")])
         _check(rc, "gt_trace_range")
+        return out
+
+    def trace_pixels(self, pixels, n_steps: int, step_precision: float, mode: int = MODE_FP64,
+                     out: Optional[dict] = None) -> dict:
+        """gt_trace_pixels: the listed flat pixels (int64 device tensor), compact outputs."""
+        n = pixels.numel()
+        if out is None:
+            out = self.alloc_outputs(n)
+        rc = self.lib.gt_trace_pixels(self.ctx, _ptr(pixels), n, int(n_steps),
+                                      float(step_precision), int(mode),
+                                      *[_ptr(out.get(k)) for k in ("t", "r", "th", "ph",
+                                                                    "status", "nsteps")])
+        _check(rc, "gt_trace_pixels")
         return out
 
     def trace_host(self, n_steps: int, step_precision: float, mode: int = MODE_FP64,

@@ -25,6 +25,7 @@ static CN operator-(CN a) { return CN(-a.v); }
 static void sincos_t(CN x, CN *s, CN *c) { g_c.sincos++; *s = CN(sin(x.v)); *c = CN(cos(x.v)); }
 static CN exp_t(CN x) { g_c.exp++; return CN(exp(x.v)); }
 static CN rsqrt_t(CN x) { g_c.rsqrt++; return CN(1.0 / sqrt(x.v)); }
+static CN rcp_t(CN x) { g_c.div++; return CN(1.0 / x.v); }
 static CN fma_t(CN a, CN b, CN c) { g_c.fma++; return CN(a.v * b.v + c.v); }
 
 #include "csrc/spacetime.cuh"

@@ -322,3 +322,16 @@ def test_graph_launch_replays_the_batch(g, tracer, oracle):
                            {k: v[sl] for k, v in direct.items()}, exclude=band)
         assert rep["agree"] >= 0.999 and rep["max_angle_escaped"] <= 1e-3, rep
         off += c.n_rays
+
+
+def test_pixel_list_trace_matches_full_image(tracer):
+    """gt_trace_pixels (compact outputs) reproduces the full-image result bitwise, in both
+    modes (FP32-mixed parks and resumes rays by their list position)."""
+    cam = W.sub_camera(W.SCHW_64, 40, 30)
+    pix = W.sample_pixels(cam.n_rays, 173, seed=9)
+    for mode, n_steps in ((0, 400000), (1, 400000)):
+        full = run_gpu(tracer, cam, n_steps, 1.5e-4, mode=mode)
+        sub = to_numpy(tracer.trace_pixels(torch.tensor(pix, device="cuda"), n_steps, 1.5e-4, mode))
+        torch.cuda.synchronize()
+        for k in ("t", "r", "th", "ph", "status", "nsteps"):
+            assert np.array_equal(sub[k], full[k][pix]), (mode, k)

@@ -55,7 +55,7 @@ struct ParkItem {
 // of the spacetime (M, spin[k] M, q[k]) with direction (alpha[k], beta[k]) in the
 // camera's (v^phi sin theta0, v^theta) plane, v^r = -1.
 struct RayParams {
-    const double *alpha, *beta, *spin, *q, *theta0; // device arrays, spin as a/M... see gt_trace_rays
+    const double *alpha, *beta, *spin, *q, *theta0; // device arrays; spin is a/M (S = spin M^2)
     double M, r0, r_switch;
 };
 

@@ -388,13 +388,14 @@ cudaError_t gemm(const __nv_bfloat16 *A, int64_t a_sm, int64_t a_sk, const __nv_
 }
 
 // Forward pass of `B` rows whose features are in X[0]; leaves Z[4] = network output.
-cudaError_t forward(gt_surrogate *s, int B, cudaStream_t st)
+// keep_pre: also store the hidden pre-activations (needed by the backward pass only).
+cudaError_t forward(gt_surrogate *s, int B, cudaStream_t st, bool keep_pre = true)
 {
     cudaError_t e = cudaSuccess;
     for (int l = 0; l < N_LAYERS && e == cudaSuccess; l++) {
         const bool last = (l == N_LAYERS - 1);
         e = gemm(s->X[l], IN_DIM[l], 1, s->wb + s->w_off[l], IN_DIM[l], 1, B, OUT_DIM[l], IN_DIM[l],
-                 s->p + s->b_off[l], last ? 0 : 1, last ? nullptr : s->Z[l],
+                 s->p + s->b_off[l], last ? 0 : 1, (last || !keep_pre) ? nullptr : s->Z[l],
                  last ? s->Z[l] : nullptr, OUT_DIM[l], false, last ? nullptr : s->X[l + 1], 1,
                  s->err, st);
     }
@@ -580,7 +581,7 @@ int gt_surrogate_eval(gt_ctx *ctx, gt_surrogate *s, int64_t n, const double *alp
         const int64_t B = n - r0 < chunk ? n - r0 : chunk;
         features_kernel<<<blocks_for(B), 256, 0, st>>>(B, r0, alpha, beta, spin, q, theta0, s->norm,
                                                        s->X[0]);
-        cudaError_t e = forward(s, (int)B, st);
+        cudaError_t e = forward(s, (int)B, st, false);
         if (e == cudaSuccess)
             e = cudaMemcpy2DAsync(out + r0 * 4, 4 * sizeof(float), s->Z[N_LAYERS - 1], 16 * sizeof(float),
                                   4 * sizeof(float), B, cudaMemcpyDeviceToDevice, st);
@@ -679,7 +680,7 @@ int infer_chunks(gt_surrogate *s, const CamDesc *d_cam, int64_t n_pix, float tau
     for (int64_t p0 = 0; p0 < n_pix; p0 += chunk) {
         const int64_t B = n_pix - p0 < chunk ? n_pix - p0 : chunk;
         camera_features_kernel<<<blocks_for(B), 256, 0, st>>>(B, p0, d_cam, s->norm, s->X[0]);
-        cudaError_t e = forward(s, (int)B, st);
+        cudaError_t e = forward(s, (int)B, st, false);
         if (e != cudaSuccess) return GT_ERR_CUDA;
         gate_kernel<<<blocks_for(B), 256, 0, st>>>(B, p0, d_cam, s->Z[N_LAYERS - 1], tau, band, t, r,
                                                    th, ph, status, nsteps, d_fallback, d_nfb);

@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A, int one_shot)
     auto load_rayparams = [&](int64_t rid, bool init) {
         CamDesc d;
         d.M = A.rays->M;
-        d.S = A.rays->spin[rid] * A.rays->M;
+        d.S = A.rays->spin[rid] * A.rays->M * A.rays->M; // spin = a/M
         d.Q = A.rays->q[rid];
         d.r0 = A.rays->r0;
         d.th0 = A.rays->theta0[rid];
@@ -597,7 +597,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A, int one_shot)
                 if (A.rays) {
                     CamDesc d;
                     d.M = A.rays->M;
-                    d.S = A.rays->spin[id] * A.rays->M;
+                    d.S = A.rays->spin[id] * A.rays->M * A.rays->M;
                     d.Q = A.rays->q[id];
                     d.r0 = A.rays->r0;
                     d.th0 = A.rays->theta0[id];

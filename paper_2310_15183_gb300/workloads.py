@@ -101,14 +101,15 @@ def batch_cameras(n_cams: int = 64, seed: int = 2310, M: float = 0.5,
 def surrogate_samples(n: int, seed: int = 15183, M: float = 0.5, fov_deg: float = 75.0,
                       r0: float = 15.0):
     """Training inputs of the surrogate: pixel direction (alpha, beta) uniform over the
-    FOV square of a camera at r0, spin a ~ U[0, 0.99M], q = 0, inclination ~ U[5, 90]
-    deg.  Returns float64 arrays (alpha, beta, a, q, theta0)."""
+    FOV square of a camera at r0, dimensionless spin a/M ~ U[0, 0.99] (S = (a/M) M^2),
+    q = 0, inclination ~ U[5, 90] deg.  Returns float64 arrays (alpha, beta, a/M, q,
+    theta0)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     V = math.tan(0.5 * fov_deg * DEG) / r0
     H = math.atan(math.tan(V))
     alpha = rng.uniform(-H, H, n)
     beta = rng.uniform(-V, V, n)
-    a = rng.uniform(0.0, 0.99 * M, n)
+    a = rng.uniform(0.0, 0.99, n)
     q = np.zeros(n)
     th0 = rng.uniform(5.0, 90.0, n) * DEG
     return alpha, beta, a, q, th0

@@ -67,10 +67,11 @@ extern "C" {
 #define GT_FLAG_COMPAT_WEIGHTS 1 /* RK4 weights 0.1667 as printed in the listing (default 1/6) */
 #define GT_FLAG_COMPAT_CAMERA 2  /* v^phi = alpha_i as in the listing (default alpha_i/sin theta0) */
 #define GT_FLAG_ONE_SHOT 4       /* one ray per thread instead of the persistent ray queue */
-#define GT_FLAG_GRAPH 8          /* issue the trace as one persistent launch replayed from a CUDA
-                                  * graph (captured once per distinct launch, cached in the
-                                  * context); FP32-mixed then keeps its FP64 zone inline, so the
-                                  * call stays asynchronous */
+#define GT_FLAG_GRAPH 8          /* replay the trace from a CUDA graph captured once per distinct
+                                  * launch and cached in the context: FP64 is one persistent
+                                  * launch; FP32-mixed runs its rounds under a conditional WHILE
+                                  * node whose condition the device sets, so the call stays
+                                  * asynchronous.  Not with GT_FLAG_ONE_SHOT. */
 
 typedef struct gt_ctx gt_ctx;
 

@@ -45,6 +45,7 @@ struct gt_ctx {
     cudaGraphExec_t graph_exec = nullptr;
     gt::TraceArgs graph_key = {};
     int graph_kmode = -1, graph_kind = -1, graph_block = 0, graph_grid = 0;
+    gt::ParkItem *graph_park = nullptr;
     // per-ray parameter block (gt_trace_rays) and surrogate fallback list
     gt::RayParams *d_rays = nullptr;
     int64_t *d_fallback = nullptr;
@@ -160,6 +161,115 @@ int grid_for(gt_ctx *c, const gt_options &e, int kmode, int kind_hint, int64_t n
     return GT_OK;
 }
 
+int ensure_park(gt_ctx *c, unsigned long long need)
+{
+    if (c->park_cap >= need) return GT_OK;
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->d_park);
+    c->d_park = nullptr;
+    c->park_cap = 0;
+    cudaError_t err = cudaMalloc(&c->d_park, 2 * need * sizeof(gt::ParkItem));
+    if (err != cudaSuccess) return cuda_code(err);
+    c->park_cap = need;
+    return GT_OK;
+}
+
+// The same rounds as one CUDA graph: FP32 launch over the fresh rays, then a WHILE node
+// whose body runs the FP64-zone launch and the FP32 continuation and sets the loop
+// condition on the device from the park count.  No host round trip.
+int build_mixed_graph(gt_ctx *c, const gt::TraceArgs &base, int kind_hint, const gt_options &e,
+                      cudaGraphExec_t *exec_out)
+{
+    int rc = ensure_park(c, (unsigned long long)base.n_rays);
+    if (rc != GT_OK) return rc;
+    gt::ParkItem *listA = c->d_park, *listB = c->d_park + c->park_cap;
+    unsigned long long *w = c->d_scratch;
+    int grid32 = 0, grid64 = 0;
+    rc = grid_for(c, e, gt::KMODE_MIXED_FP32, kind_hint, base.n_rays, false, &grid32);
+    if (rc == GT_OK) rc = grid_for(c, e, gt::KMODE_ZONE_FP64, kind_hint, base.n_rays, false, &grid64);
+    if (rc != GT_OK) return rc;
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle h;
+    cudaError_t err = cudaGraphCreate(&g, 0);
+    if (err == cudaSuccess) err = cudaGraphConditionalHandleCreate(&h, g, 0, 0);
+    if (err != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_code(err);
+    }
+    const size_t W8 = sizeof(unsigned long long);
+    cudaStream_t cs = c->cap_stream;
+    // prologue: first FP32 round and the initial condition, then the WHILE node
+    err = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    cudaGraph_t body = nullptr;
+    if (err == cudaSuccess) {
+        cudaError_t e1 = cudaMemsetAsync(w, 0, gt::SCR_WORDS * W8, cs);
+        gt::TraceArgs a = base;
+        a.in_items = listB;
+        a.in_count = w + gt::SCR_TO32;
+        a.in_cap = c->park_cap;
+        a.out_items = listA;
+        a.out_count = w + gt::SCR_TO64;
+        a.out_cap = c->park_cap;
+        if (e1 == cudaSuccess)
+            e1 = gt::launch_trace(a, gt::KMODE_MIXED_FP32, kind_hint, e.block_size, grid32, false, cs);
+        if (e1 == cudaSuccess) e1 = gt::launch_set_condition(h, w + gt::SCR_TO64, cs);
+        cudaStreamCaptureStatus cst;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t nd = 0;
+        cudaGraph_t gg = nullptr;
+        if (e1 == cudaSuccess) e1 = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &gg, &deps, nullptr, &nd);
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cn = nullptr;
+        if (e1 == cudaSuccess) e1 = cudaGraphAddNode(&cn, gg, deps, nullptr, nd, &cp);
+        if (e1 == cudaSuccess) {
+            body = cp.conditional.phGraph_out[0];
+            e1 = cudaStreamUpdateCaptureDependencies(cs, &cn, nullptr, 1,
+                                                     cudaStreamSetCaptureDependencies);
+        }
+        cudaGraph_t done = nullptr;
+        err = cudaStreamEndCapture(cs, &done);
+        if (err == cudaSuccess) err = e1;
+    }
+    // body: FP64 zone round A -> B, FP32 round B -> A, condition from A's count
+    if (err == cudaSuccess && body)
+        err = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeThreadLocal);
+    if (err == cudaSuccess && body) {
+        gt::TraceArgs a = base;
+        a.n_fresh = 0;
+        a.in_cap = a.out_cap = c->park_cap;
+        cudaError_t e1 = cudaMemsetAsync(w + gt::SCR_NEXT_RAY, 0, W8, cs);
+        if (e1 == cudaSuccess) e1 = cudaMemsetAsync(w + gt::SCR_TO32, 0, W8, cs);
+        a.in_items = listA;
+        a.in_count = w + gt::SCR_TO64;
+        a.out_items = listB;
+        a.out_count = w + gt::SCR_TO32;
+        if (e1 == cudaSuccess)
+            e1 = gt::launch_trace(a, gt::KMODE_ZONE_FP64, kind_hint, e.block_size, grid64, false, cs);
+        if (e1 == cudaSuccess) e1 = cudaMemsetAsync(w + gt::SCR_NEXT_RAY, 0, W8, cs);
+        if (e1 == cudaSuccess) e1 = cudaMemsetAsync(w + gt::SCR_TO64, 0, W8, cs);
+        a.in_items = listB;
+        a.in_count = w + gt::SCR_TO32;
+        a.out_items = listA;
+        a.out_count = w + gt::SCR_TO64;
+        if (e1 == cudaSuccess)
+            e1 = gt::launch_trace(a, gt::KMODE_MIXED_FP32, kind_hint, e.block_size, grid32, false, cs);
+        if (e1 == cudaSuccess) e1 = gt::launch_set_condition(h, w + gt::SCR_TO64, cs);
+        cudaGraph_t done = nullptr;
+        err = cudaStreamEndCapture(cs, &done);
+        if (err == cudaSuccess) err = e1;
+    } else if (err == cudaSuccess) {
+        err = cudaErrorUnknown;
+    }
+    if (err == cudaSuccess) err = cudaGraphInstantiate(exec_out, g, 0);
+    cudaGraphDestroy(g);
+    return cuda_code(err);
+}
+
 // FP32-mixed runs in rounds on the context's stream: an FP32 launch over the fresh rays
 // parks every ray that enters the FP64 zone; an FP64 launch integrates the parked rays
 // until they leave the zone (parked again) or stop; an FP32 launch continues the
@@ -167,16 +277,8 @@ int grid_for(gt_ctx *c, const gt_options &e, int kmode, int kind_hint, int64_t n
 // between rounds, so this mode returns after the work has completed.
 int run_mixed_rounds(gt_ctx *c, gt::TraceArgs &a, int kind_hint, const gt_options &e, bool one_shot)
 {
-    const unsigned long long need = (unsigned long long)a.n_rays;
-    if (c->park_cap < need) {
-        cudaStreamSynchronize(c->stream);
-        cudaFree(c->d_park);
-        c->d_park = nullptr;
-        c->park_cap = 0;
-        cudaError_t err = cudaMalloc(&c->d_park, 2 * need * sizeof(gt::ParkItem));
-        if (err != cudaSuccess) return cuda_code(err);
-        c->park_cap = need;
-    }
+    int prc = ensure_park(c, (unsigned long long)a.n_rays);
+    if (prc != GT_OK) return prc;
     gt::ParkItem *listA = c->d_park, *listB = c->d_park + c->park_cap;
     unsigned long long *w = c->d_scratch;
     a.out_cap = c->park_cap;
@@ -269,15 +371,18 @@ int run_trace(gt_ctx *c, const CamDesc *d_cams, int n_cams, int kind_hint, int64
     const bool one_shot = (e.flags & GT_FLAG_ONE_SHOT) != 0;
     int rc;
     if (e.flags & GT_FLAG_GRAPH) {
-        // one persistent launch (FP32-mixed with its FP64 zone inline) replayed from a
-        // CUDA graph; the graph is captured once per distinct launch and cached
-        const int kmode = mode == GT_MODE_FP64 ? gt::KMODE_FP64 : gt::KMODE_MIXED_INLINE;
+        // the launch replayed from a CUDA graph, captured once per distinct launch and
+        // cached: FP64 is one persistent launch; FP32-mixed is its rounds under a WHILE
+        // node whose condition the device sets from the park count
+        const int kmode = mode == GT_MODE_FP64 ? gt::KMODE_FP64 : gt::KMODE_MIXED_FP32;
+        if (one_shot) return GT_ERR_INVALID_ARG; // graphs replay the persistent launch
         int grid;
         rc = grid_for(c, e, kmode, kind_hint, n_rays, one_shot, &grid);
         if (rc != GT_OK) return rc;
         const bool same = c->graph_exec && memcmp(&c->graph_key, &a, sizeof a) == 0 &&
                           c->graph_kmode == kmode && c->graph_kind == kind_hint &&
-                          c->graph_block == e.block_size && c->graph_grid == grid;
+                          c->graph_block == e.block_size && c->graph_grid == grid &&
+                          c->graph_park == c->d_park && c->park_cap >= (unsigned long long)n_rays;
         if (!same) {
             if (!c->cap_stream) {
                 err = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
@@ -287,24 +392,34 @@ int run_trace(gt_ctx *c, const CamDesc *d_cams, int n_cams, int kind_hint, int64
                 cudaGraphExecDestroy(c->graph_exec);
                 c->graph_exec = nullptr;
             }
-            cudaGraph_t graph = nullptr;
-            err = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
-            if (err != cudaSuccess) return cuda_code(err);
-            cudaError_t e1 = cudaMemsetAsync(c->d_scratch, 0,
-                                             gt::SCR_WORDS * sizeof(unsigned long long), c->cap_stream);
-            cudaError_t e2 = gt::launch_trace(a, kmode, kind_hint, e.block_size, grid, one_shot,
-                                              c->cap_stream);
-            err = cudaStreamEndCapture(c->cap_stream, &graph);
-            if (e1 != cudaSuccess || e2 != cudaSuccess || err != cudaSuccess) {
-                if (graph) cudaGraphDestroy(graph);
-                return GT_ERR_CUDA;
+            if (kmode == gt::KMODE_FP64) {
+                cudaGraph_t graph = nullptr;
+                err = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+                if (err != cudaSuccess) return cuda_code(err);
+                cudaError_t e1 = cudaMemsetAsync(c->d_scratch, 0,
+                                                 gt::SCR_WORDS * sizeof(unsigned long long),
+                                                 c->cap_stream);
+                cudaError_t e2 = gt::launch_trace(a, kmode, kind_hint, e.block_size, grid,
+                                                  one_shot, c->cap_stream);
+                err = cudaStreamEndCapture(c->cap_stream, &graph);
+                if (e1 != cudaSuccess || e2 != cudaSuccess || err != cudaSuccess) {
+                    if (graph) cudaGraphDestroy(graph);
+                    return GT_ERR_CUDA;
+                }
+                err = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+                cudaGraphDestroy(graph);
+                if (err != cudaSuccess) {
+                    c->graph_exec = nullptr;
+                    return cuda_code(err);
+                }
+            } else {
+                rc = build_mixed_graph(c, a, kind_hint, e, &c->graph_exec);
+                if (rc != GT_OK) {
+                    c->graph_exec = nullptr;
+                    return rc;
+                }
             }
-            err = cudaGraphInstantiate(&c->graph_exec, graph, 0);
-            cudaGraphDestroy(graph);
-            if (err != cudaSuccess) {
-                c->graph_exec = nullptr;
-                return cuda_code(err);
-            }
+            c->graph_park = c->d_park;
             c->graph_key = a;
             c->graph_kmode = kmode;
             c->graph_kind = kind_hint;

@@ -90,6 +90,9 @@ struct TraceArgs {
 // Launchers (trace.cu).  Return a cudaError_t from the launch.
 cudaError_t launch_camera_setup(CamDesc *d_cams, int n_cams, int flags, double r_switch,
                                 cudaStream_t s);
+// One-thread kernel setting a graph WHILE node's condition to (*count != 0).
+cudaError_t launch_set_condition(cudaGraphConditionalHandle h, const unsigned long long *count,
+                                 cudaStream_t s);
 // Resident blocks per SM of the trace kernel for this block size (>= 1).
 int max_blocks_per_sm(int kmode, int kind_hint, int block);
 cudaError_t launch_trace(const TraceArgs &a, int kmode, int kind_hint, int block, int grid,

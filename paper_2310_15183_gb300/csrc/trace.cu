@@ -621,6 +621,20 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A, int one_shot)
     }
 }
 
+// Loop condition of the graph-resident FP32-mixed rounds: continue while rays are parked.
+__global__ void set_loop_condition_kernel(cudaGraphConditionalHandle h,
+                                          const unsigned long long *count)
+{
+    cudaGraphSetConditional(h, *count != 0ull ? 1u : 0u);
+}
+
+cudaError_t launch_set_condition(cudaGraphConditionalHandle h, const unsigned long long *count,
+                                 cudaStream_t s)
+{
+    set_loop_condition_kernel<<<1, 1, 0, s>>>(h, count);
+    return cudaGetLastError();
+}
+
 template <int MODE, int KIND>
 static cudaError_t launch_one(const TraceArgs &a, int block, int grid, bool one_shot, cudaStream_t s)
 {

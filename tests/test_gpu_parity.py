@@ -294,9 +294,10 @@ def test_autotuner_picks_valid_shape_caches_it_and_keeps_bits(g, tracer, tmp_pat
 
 
 def test_graph_launch_replays_the_batch(g, tracer, oracle):
-    """GT_FLAG_GRAPH: the batched trace as one persistent launch replayed from a cached
-    CUDA graph -- FP64 bitwise equal to the direct launch, twice in a row; FP32-mixed
-    (FP64 zone inline) within the mixed-precision criteria."""
+    """GT_FLAG_GRAPH: the batched trace replayed from a cached CUDA graph -- FP64 bitwise
+    equal to the direct launch, twice in a row; FP32-mixed (rounds under a conditional
+    WHILE node) bitwise equal to the host-driven rounds and within the mixed-precision
+    criteria of FP64."""
     cams = [W.Camera(0.5, 0.1, 0.0, 12.0, 0.7, 75.0, 13, 9),
             W.Camera(0.5, 0.2475, 0.0, 20.0, 1.5, 60.0, 5, 17),
             W.Camera(0.5, 0.24, 0.0, 15.0, 80 * W.DEG, 30.0, 12, 10)]
@@ -314,6 +315,10 @@ def test_graph_launch_replays_the_batch(g, tracer, oracle):
     mixed = to_numpy(tracer.trace_batch(cams, 300000, 1.5e-4, 1))
     torch.cuda.synchronize()
     tracer.set_options()
+    rounds = to_numpy(tracer.trace_batch(cams, 300000, 1.5e-4, 1))
+    torch.cuda.synchronize()
+    for key in ("t", "r", "th", "ph", "status", "nsteps"):  # same kernels, same bits
+        assert np.array_equal(mixed[key], rounds[key]), key
     off = 0
     for c in cams:
         sl = slice(off, off + c.n_rays)

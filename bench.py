@@ -98,6 +98,32 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ------------------------------------------------------------------ ncu traffic record
+def source_sha1() -> str:
+    """Hash of the CUDA sources and the C ABI header (identifies the kernel build)."""
+    import glob
+    import hashlib
+    h = hashlib.sha1()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_2310_15183_gb300", "csrc", "*.cu*")) +
+                   glob.glob(os.path.join(ROOT, "include", "*.h")))
+    for f in files:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel: str, rays: int):
+    """DRAM bytes per launch of `kernel` scaled from the committed ncu capture record
+    (profiles/traffic.json), or None when the kernel sources changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path)).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("source_sha1") != source_sha1():
+        return None
+    return rec["dram_bytes_per_ray"] * rays
+
+
 # ------------------------------------------------------------------ CPU oracle
 def oracle_rate(wl: W.Workload, target_s: float = 12.0, seed: int = 3) -> dict:
     """Time the FP64 oracle, as it stands, on a bounded pixel sample of the workload."""
@@ -224,8 +250,8 @@ def leg_surrogate(tr, geotrace, args, torch):
     labels = [lab["status"], lab["th"], lab["ph"]]
     sg = geotrace.Surrogate(0, r0=r0, seed=7)
     t0 = time.perf_counter()
-    losses = sg.train(tr, dev, labels, epochs=args.sg_epochs, batch=4096, lr=2e-3,
-                      dir_weight=10.0)
+    losses = sg.train(tr, dev, labels, epochs=args.sg_epochs, batch=args.sg_batch, lr=2e-3,
+                      dir_weight=args.sg_dir_weight)
     t_train = time.perf_counter() - t0
     cam = W.Camera(M=M, S=0.9 * M * M, Q=0.0, r0=r0, theta0=80 * W.DEG, fov_deg=75.0,
                    res_x=args.sg_res, res_y=args.sg_res)
@@ -234,7 +260,8 @@ def leg_surrogate(tr, geotrace, args, torch):
     tr.set_options()
     res = {"train_rays": args.sg_samples, "label_seconds": t_label,
            "label_steps_per_s": _steps(lab) / t_label, "train_seconds": t_train,
-           "epochs": args.sg_epochs, "loss_first_last": [float(losses[0]), float(losses[-1])],
+           "epochs": args.sg_epochs, "batch": args.sg_batch, "dir_weight": args.sg_dir_weight,
+           "loss_first_last": [float(losses[0]), float(losses[-1])],
            "image": [cam.res_x, cam.res_y]}
     step = max(1, cam.res_x // 64)
     jj, ii = np.meshgrid(np.arange(step // 2, cam.res_y, step), np.arange(step // 2, cam.res_x, step),
@@ -284,6 +311,51 @@ def leg_surrogate(tr, geotrace, args, torch):
     res["integrator_subsample"] = f"{sub_pix.numel()} pixels (every {sub_step}th in x and y)"
     res["judge"] = f"FP64 integrator on {judge_pix.size} pixels (every {step}th in x and y)"
     sg.close()
+    return res
+
+
+def leg_gemm(geotrace, args, torch):
+    """tcgen05 BF16 GEMM at the surrogate's hidden-layer shape (M = 2^20 rows, N = K = 256,
+    bias + SiLU epilogue, bf16 output) and at its weight-gradient shape (M = N = 256,
+    K = 2^16, split-K), timed with CUDA events; fraction of the measured bf16 peak."""
+    import ctypes
+    lib = geotrace.load_library()
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1900.0}
+    peak = peaks.get("bf16_tflops", 1900.0)
+    res = {"peak_tflops": peak, "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)"}
+    g = torch.Generator(device="cuda").manual_seed(1)
+    for name, (M, N, K, splits, bn) in {"forward_hidden": (1 << 20, 256, 256, 1, 256),
+                                        "weight_grad": (256, 256, 1 << 16, 128, 256)}.items():
+        A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+        B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+        C = torch.zeros(M, N, device="cuda", dtype=torch.float32)
+        bias = torch.zeros(N, device="cuda", dtype=torch.float32)
+        act = 1 if splits == 1 else 0
+
+        def run():
+            if splits > 1:
+                C.zero_()
+            rc = lib.gt_gemm_bf16(0, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream),
+                                  M, N, K, ctypes.c_void_p(A.data_ptr()), K, 1,
+                                  ctypes.c_void_p(B.data_ptr()), K, 1,
+                                  ctypes.c_void_p(bias.data_ptr()) if act else None, act,
+                                  ctypes.c_void_p(C.data_ptr()), N, int(splits > 1), splits, bn)
+            assert rc == 0
+        for _ in range(3):
+            run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 10
+        e0.record()
+        for _ in range(reps):
+            run()
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / reps
+        tf = 2.0 * M * N * K / t / 1e12
+        res[name] = {"M": M, "N": N, "K": K, "splits": splits, "seconds": t, "tflops": tf,
+                     "frac_of_peak": tf / peak}
     return res
 
 
@@ -343,7 +415,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--legs", default="", help="extra legs: batch,surrogate,sweep (comma list)")
     ap.add_argument("--sg-samples", type=int, default=1 << 22)
-    ap.add_argument("--sg-epochs", type=int, default=12)
+    ap.add_argument("--sg-epochs", type=int, default=40)
+    ap.add_argument("--sg-batch", type=int, default=16384)
+    ap.add_argument("--sg-dir-weight", type=float, default=30.0)
     ap.add_argument("--sg-res", type=int, default=4096)
     ap.add_argument("--batch-scale", type=int, default=8,
                     help="batch leg: camera sides divided by this factor")
@@ -433,8 +507,10 @@ def main():
         peak = FP64_NOMINAL
         peak_note = "FP64 dense 1.25 TFLOP/s (nominal)"
         measured_peak = geotrace.measure_fma_peak(local, fp64=True, iters=200)
+    kname = f"trace_kernel<{2 if mode else 0},{1 if cam.Q != 0 else 0}>"
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": measured_traffic(kname, n), "kernel": kname,
                 "peak_source": peak_note, "measured_fma_peak": measured_peak / 1e12,
                 "frac_of_measured_fma_peak": achieved / measured_peak,
                 "flops_per_rk4_step": flops_per_step,
@@ -505,6 +581,8 @@ def main():
             legs["surrogate"] = leg_surrogate(tr, geotrace, args, torch)
         elif leg == "sweep":
             legs["sweep"] = leg_sweep(tr, geotrace, args, torch)
+        elif leg == "gemm":
+            legs["gemm"] = leg_gemm(geotrace, args, torch)
         else:
             raise SystemExit(f"unknown leg {leg}")
         legs[leg]["leg_wall_s"] = time.perf_counter() - t0

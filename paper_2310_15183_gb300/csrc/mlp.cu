@@ -172,6 +172,7 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(GemmArgs g)
                             *p = y;
                     }
                     if (g.C16) g.C16[(int64_t)row * g.ldc16 + col] = __float2bfloat16(y);
+                    if (g.C16T) g.C16T[(int64_t)col * g.ldt + row] = __float2bfloat16(y);
                 }
             }
         }
@@ -179,6 +180,165 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(GemmArgs g)
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, NCOLS);
+}
+
+
+// ---------------------------------------------------------------------------------
+// Pipelined variant for K-contiguous operands (a_sk = b_sk = 1, 16-byte aligned rows):
+// every thread moves 16-byte pieces straight into the K-major core-matrix layout with
+// cp.async (zero-filled beyond the matrix edges), STAGES chunks in flight; one thread
+// issues the MMAs of a chunk as soon as it has landed and commits them to the stage's
+// mbarrier, which gates the stage's reuse.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                 "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N)); }
+
+__device__ __forceinline__ void issue_tile(uint32_t s_base, const __nv_bfloat16 *__restrict__ src,
+                                           int rows_total, int k_total, int64_t s_row, int row0,
+                                           int k0, int nrows, uint32_t lbo)
+{
+    const int npieces = nrows * (BK / 8);
+    for (int v = threadIdx.x; v < npieces; v += blockDim.x) {
+        const int row = v >> 3, kb = v & 7; // BK / 8 == 8 pieces per row
+        const int gr = row0 + row, gk = k0 + kb * 8;
+        int bytes = 0;
+        const __nv_bfloat16 *p = src;
+        if (gr < rows_total && gk < k_total) {
+            bytes = (k_total - gk) >= 8 ? 16 : (k_total - gk) * 2;
+            p = src + (int64_t)gr * s_row + gk;
+        }
+        cp_async16(s_base + tc::kmajor_offset(row, kb * 8, lbo), p, (uint32_t)bytes);
+    }
+}
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(128) tc_gemm_pipe_kernel(GemmArgs g)
+{
+    using L = GemmSmem<BN>;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + STAGES * L::STAGE);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + STAGES * L::STAGE + 8 * STAGES);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    constexpr uint32_t NCOLS = BN < 32 ? 32 : BN;
+    const int nk_total = (g.K + BK - 1) / BK;
+    const int per = (nk_total + gridDim.z - 1) / gridDim.z;
+    const int c_begin = blockIdx.z * per;
+    const int c_end = min(nk_total, c_begin + per);
+    const int nk = c_end > c_begin ? c_end - c_begin : 0;
+
+    if (warp == 0) tc::tmem_alloc(tc::smem_u32(tmem_slot), NCOLS);
+    if (tid == 0) {
+        for (int st = 0; st < STAGES; st++) tc::mbar_init(tc::smem_u32(&mbar[st]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t sbase = tc::smem_u32(smem);
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+
+    auto issue = [&](int c) {
+        const uint32_t a_s = sbase + (c % STAGES) * L::STAGE;
+        const int k0 = (c_begin + c) * BK;
+        issue_tile(a_s, g.A, g.M, g.K, g.a_sm, m0, k0, BM, L::A_LBO);
+        issue_tile(a_s + L::A_BYTES, g.B, g.N, g.K, g.b_sn, n0, k0, BN, L::B_LBO);
+    };
+#pragma unroll
+    for (int c = 0; c < STAGES - 1; c++) {
+        if (c < nk) issue(c);
+        cp_async_commit();
+    }
+    bool ok = true;
+    for (int c = 0; c < nk; ++c) {
+        cp_async_wait<STAGES - 2>(); // this thread's pieces of chunk c have landed
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t a_base = sbase + (c % STAGES) * L::STAGE, b_base = a_base + L::A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+                const uint64_t ad = tc::smem_desc(a_base + kk * 2 * L::A_LBO, L::A_LBO, 128);
+                const uint64_t bd = tc::smem_desc(b_base + kk * 2 * L::B_LBO, L::B_LBO, 128);
+                tc::mma_bf16(tmem, ad, bd, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+            }
+            tc::mma_commit(tc::smem_u32(&mbar[c % STAGES]));
+        }
+        const int nc = c + STAGES - 1;
+        if (c >= 1 && nc < nk) { // chunk nc reuses the stage of chunk c - 1
+            ok = tc::mbar_wait(tc::smem_u32(&mbar[(c - 1) % STAGES]),
+                               (uint32_t)(((c - 1) / STAGES) & 1), WAIT_LIMIT);
+            if (!ok) break;
+        }
+        if (nc < nk) issue(nc);
+        cp_async_commit();
+    }
+    cp_async_wait<0>();
+    if (ok && nk > 0) {
+        const int last = nk - 1;
+        ok = tc::mbar_wait(tc::smem_u32(&mbar[last % STAGES]), (uint32_t)((last / STAGES) & 1),
+                           WAIT_LIMIT);
+    }
+    __syncthreads();
+    tc::fence_after_sync();
+    if (!ok) {
+        if (tid == 0 && g.err) atomicExch(g.err, 1);
+    } else {
+        const int row = m0 + warp * 32 + lane;
+        for (int cc = 0; cc < BN; cc += 32) {
+            float v[32];
+            if (nk > 0) {
+                tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc, v);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 32; i++) v[i] = 0.0f;
+            }
+            if (row < g.M) {
+#pragma unroll
+                for (int i = 0; i < 32; i++) {
+                    const int col = n0 + cc + i;
+                    if (cc + i >= BN || col >= g.N) continue;
+                    float z = v[i];
+                    if (g.bias && blockIdx.z == 0) z += g.bias[col];
+                    if (g.pre) g.pre[(int64_t)row * g.ld_pre + col] = z;
+                    const float y = g.act == 1 ? silu(z) : z;
+                    if (g.C32) {
+                        float *p = g.C32 + (int64_t)row * g.ldc + col;
+                        if (g.atomic)
+                            atomicAdd(p, y);
+                        else
+                            *p = y;
+                    }
+                    if (g.C16) g.C16[(int64_t)row * g.ldc16 + col] = __float2bfloat16(y);
+                    if (g.C16T) g.C16T[(int64_t)col * g.ldt + row] = __float2bfloat16(y);
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, NCOLS);
+}
+
+template <int BN>
+cudaError_t launch_pipe(const GemmArgs &g, int splits, cudaStream_t s)
+{
+    using L = GemmSmem<BN>;
+    constexpr int STAGES = 4;
+    const uint32_t bytes = STAGES * L::STAGE + 8 * STAGES + 64;
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_pipe_kernel<BN, STAGES>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    dim3 grid((g.M + BM - 1) / BM, (g.N + BN - 1) / BN, splits);
+    tc_gemm_pipe_kernel<BN, STAGES><<<grid, 128, bytes, s>>>(g);
+    return cudaGetLastError();
 }
 
 template <int BN>
@@ -198,6 +358,18 @@ cudaError_t launch_bn(const GemmArgs &g, int splits, cudaStream_t s)
 cudaError_t launch_gemm(const GemmArgs &g, int bn, int splits, cudaStream_t s)
 {
     if (splits < 1) splits = 1;
+    const bool pipe = g.a_sk == 1 && g.b_sk == 1 && g.a_sm % 8 == 0 && g.b_sn % 8 == 0 &&
+                      ((uintptr_t)g.A % 16) == 0 && ((uintptr_t)g.B % 16) == 0;
+    if (pipe) {
+        switch (bn) {
+        case 16: return launch_pipe<16>(g, splits, s);
+        case 32: return launch_pipe<32>(g, splits, s);
+        case 64: return launch_pipe<64>(g, splits, s);
+        case 128: return launch_pipe<128>(g, splits, s);
+        case 256: return launch_pipe<256>(g, splits, s);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     switch (bn) {
     case 16: return launch_bn<16>(g, splits, s);
     case 32: return launch_bn<32>(g, splits, s);

@@ -22,6 +22,8 @@ struct GemmArgs {
     int atomic;        // accumulate into C32 with atomics (split-K)
     __nv_bfloat16 *C16; // optional bf16 output (ldc16)
     int64_t ldc16;
+    __nv_bfloat16 *C16T; // optional transposed bf16 output: C16T[n * ldt + m]
+    int64_t ldt;
     int *err;          // set to 1 when an mbarrier wait ran out
 };
 

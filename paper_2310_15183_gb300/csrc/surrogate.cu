@@ -59,7 +59,7 @@ __global__ void init_params_kernel(float *p, int64_t n, const int64_t *offs, con
 // features of samples [row0, row0 + n): X0[r, 0..15] (bf16)
 __global__ void features_kernel(int64_t n, int64_t row0, const double *alpha, const double *beta,
                                 const double *spin, const double *q, const double *theta0,
-                                Norm nm, __nv_bfloat16 *X0)
+                                Norm nm, __nv_bfloat16 *X0, __nv_bfloat16 *X0T = nullptr)
 {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
@@ -74,6 +74,9 @@ __global__ void features_kernel(int64_t n, int64_t row0, const double *alpha, co
     for (int j = 5; j < 16; j++) f[j] = 0.0f;
 #pragma unroll
     for (int j = 0; j < 16; j++) X0[r * 16 + j] = __float2bfloat16(f[j]);
+    if (X0T)
+#pragma unroll
+        for (int j = 0; j < 16; j++) X0T[j * n + r] = __float2bfloat16(f[j]);
 }
 
 // features of camera pixels [pix0, pix0 + n) (flat j*res_x + i)
@@ -103,7 +106,7 @@ __global__ void camera_features_kernel(int64_t n, int64_t pix0, const CamDesc *c
 // labels: [B x 4] = (y, dx, dy, dz).  Writes dZ5 (fp32 and bf16, 16 columns, zeros
 // beyond 4) and accumulates the loss sum.
 __global__ void head_kernel(int B, const float *Z5, const float *labels, float w_dir, float inv_b,
-                            float *dZ5f, __nv_bfloat16 *dZ5b, float *loss_acc)
+                            float *dZ5f, __nv_bfloat16 *dZ5b, __nv_bfloat16 *dZ5T, float *loss_acc)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     float l = 0.0f;
@@ -125,6 +128,7 @@ __global__ void head_kernel(int B, const float *Z5, const float *labels, float w
         for (int j = 0; j < 16; j++) {
             dZ5f[(int64_t)r * 16 + j] = g[j];
             dZ5b[(int64_t)r * 16 + j] = __float2bfloat16(g[j]);
+            dZ5T[(int64_t)j * B + r] = __float2bfloat16(g[j]);
         }
     }
     // warp-reduce the loss, one atomic per warp
@@ -133,16 +137,31 @@ __global__ void head_kernel(int B, const float *Z5, const float *labels, float w
 }
 
 // dZ = dX * SiLU'(Z), SiLU'(z) = s (1 + z (1 - s)), s = sigmoid(z)
-__global__ void silu_backward_kernel(int64_t n, const float *dX, const float *Z, float *dZf,
-                                     __nv_bfloat16 *dZb)
+// dZT is the transposed (cols x rows) bf16 copy used by the weight-gradient product.
+__global__ void silu_backward_kernel(int64_t rows, int cols, const float *dX, const float *Z,
+                                     float *dZf, __nv_bfloat16 *dZb, __nv_bfloat16 *dZT)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    // consecutive threads take consecutive rows of one column: coalesced transposed stores
+    const int64_t n = rows * cols;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t r = k % rows, c = k / rows;
+    const int64_t i = r * cols + c;
     const float z = Z[i];
     const float s = sigmoidf(z);
     const float g = dX[i] * s * (1.0f + z * (1.0f - s));
     dZf[i] = g;
     dZb[i] = __float2bfloat16(g);
+    dZT[c * rows + r] = __float2bfloat16(g);
+}
+
+// WT[l] = bf16 transpose of the fp32 weights [out][in] -> [in][out]
+__global__ void weights_t_kernel(const float *W, int out_dim, int in_dim, __nv_bfloat16 *WT)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= out_dim * in_dim) return;
+    const int o = k / in_dim, i = k % in_dim;
+    WT[(int64_t)i * out_dim + o] = __float2bfloat16(W[k]);
 }
 
 // out[c] += sum_r M[r, c]  (rows x cols, row-major)
@@ -298,6 +317,9 @@ struct gt_surrogate {
     // workspace for `rows` rows
     int64_t rows = 0;
     __nv_bfloat16 *X[N_LAYERS] = {}; // inputs of each layer (bf16)
+    __nv_bfloat16 *XT[N_LAYERS] = {}; // the same, transposed (in_dim x rows)
+    __nv_bfloat16 *WT = nullptr;      // transposed bf16 weights ([in][out] per layer)
+    __nv_bfloat16 *dZT = nullptr;     // transposed bf16 gradient (cols x rows)
     float *Z[N_LAYERS] = {};         // pre-activations (fp32)
     float *dXf = nullptr, *dZf = nullptr, *lab = nullptr, *loss = nullptr;
     __nv_bfloat16 *dZb = nullptr;
@@ -310,10 +332,14 @@ void free_ws(gt_surrogate *s)
 {
     for (int l = 0; l < N_LAYERS; l++) {
         cudaFree(s->X[l]);
+        cudaFree(s->XT[l]);
         cudaFree(s->Z[l]);
         s->X[l] = nullptr;
+        s->XT[l] = nullptr;
         s->Z[l] = nullptr;
     }
+    cudaFree(s->dZT);
+    s->dZT = nullptr;
     cudaFree(s->dXf);
     cudaFree(s->dZf);
     cudaFree(s->dZb);
@@ -330,11 +356,13 @@ int ensure_ws(gt_surrogate *s, int64_t rows)
     cudaError_t e = cudaSuccess;
     for (int l = 0; l < N_LAYERS && e == cudaSuccess; l++) {
         e = cudaMalloc(&s->X[l], rows * IN_DIM[l] * sizeof(__nv_bfloat16));
+        if (e == cudaSuccess) e = cudaMalloc(&s->XT[l], rows * IN_DIM[l] * sizeof(__nv_bfloat16));
         if (e == cudaSuccess) e = cudaMalloc(&s->Z[l], rows * OUT_DIM[l] * sizeof(float));
     }
     if (e == cudaSuccess) e = cudaMalloc(&s->dXf, rows * 256 * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&s->dZf, rows * 256 * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&s->dZb, rows * 256 * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMalloc(&s->dZT, rows * 256 * sizeof(__nv_bfloat16));
     if (e == cudaSuccess) e = cudaMalloc(&s->lab, rows * 4 * sizeof(float));
     if (e != cudaSuccess) {
         free_ws(s);
@@ -361,7 +389,7 @@ struct Dev {
 cudaError_t gemm(const __nv_bfloat16 *A, int64_t a_sm, int64_t a_sk, const __nv_bfloat16 *B,
                  int64_t b_sn, int64_t b_sk, int M, int N, int K, const float *bias, int act,
                  float *pre, float *C32, int64_t ldc, bool atomic, __nv_bfloat16 *C16, int splits,
-                 int *err, cudaStream_t st)
+                 int *err, cudaStream_t st, __nv_bfloat16 *C16T = nullptr)
 {
     GemmArgs g = {};
     g.M = M;
@@ -382,6 +410,8 @@ cudaError_t gemm(const __nv_bfloat16 *A, int64_t a_sm, int64_t a_sk, const __nv_
     g.atomic = atomic ? 1 : 0;
     g.C16 = C16;
     g.ldc16 = N;
+    g.C16T = C16T;
+    g.ldt = M;
     g.err = err;
     const int bn = N >= 256 ? 256 : (N >= 128 ? 128 : (N >= 64 ? 64 : (N >= 32 ? 32 : 16)));
     return launch_gemm(g, bn, splits, st);
@@ -397,7 +427,7 @@ cudaError_t forward(gt_surrogate *s, int B, cudaStream_t st, bool keep_pre = tru
         e = gemm(s->X[l], IN_DIM[l], 1, s->wb + s->w_off[l], IN_DIM[l], 1, B, OUT_DIM[l], IN_DIM[l],
                  s->p + s->b_off[l], last ? 0 : 1, (last || !keep_pre) ? nullptr : s->Z[l],
                  last ? s->Z[l] : nullptr, OUT_DIM[l], false, last ? nullptr : s->X[l + 1], 1,
-                 s->err, st);
+                 s->err, st, (last || !keep_pre) ? nullptr : s->XT[l + 1]);
     }
     return e;
 }
@@ -408,23 +438,24 @@ cudaError_t backward(gt_surrogate *s, int B, float w_dir, cudaStream_t st)
     cudaError_t e = cudaMemsetAsync(s->g, 0, s->n_params * sizeof(float), st);
     if (e != cudaSuccess) return e;
     head_kernel<<<blocks_for(B), 256, 0, st>>>(B, s->Z[N_LAYERS - 1], s->lab, w_dir, 1.0f / B,
-                                               s->dZf, s->dZb, s->loss);
+                                               s->dZf, s->dZb, s->dZT, s->loss);
     for (int l = N_LAYERS - 1; l >= 0 && e == cudaSuccess; l--) {
         const int N = OUT_DIM[l], K = IN_DIM[l];
-        // dW_l[n, k] = sum_b dZ[b, n] X_l[b, k]   (split over the batch)
-        const int splits = B >= 4096 ? (B / 2048 < 64 ? B / 2048 : 64) : 1;
-        e = gemm(s->dZb, 1, N, s->X[l], 1, K, N, K, B, nullptr, 0, nullptr, s->g + s->w_off[l], K,
+        // dW_l[n, k] = sum_b dZ[b, n] X_l[b, k] from the transposed copies (K-contiguous
+        // in the batch), split over the batch
+        const int splits = B >= 512 ? (B / 256 < 128 ? B / 256 : 128) : 1;
+        e = gemm(s->dZT, B, 1, s->XT[l], B, 1, N, K, B, nullptr, 0, nullptr, s->g + s->w_off[l], K,
                  true, nullptr, splits, s->err, st);
         if (e != cudaSuccess) break;
         // db_l = column sums of dZ
         colsum_kernel<<<dim3(blocks_for(N, 128), 64), 128, 0, st>>>(s->dZf, B, N, s->g + s->b_off[l]);
         if (l == 0) break;
-        // dX[b, k] = sum_n dZ[b, n] W_l[n, k]
-        e = gemm(s->dZb, N, 1, s->wb + s->w_off[l], 1, K, B, K, N, nullptr, 0, nullptr, s->dXf, K,
+        // dX[b, k] = sum_n dZ[b, n] W_l[n, k] = dZ . (W_l^T)^T
+        e = gemm(s->dZb, N, 1, s->WT + s->w_off[l], N, 1, B, K, N, nullptr, 0, nullptr, s->dXf, K,
                  false, nullptr, 1, s->err, st);
         if (e != cudaSuccess) break;
-        silu_backward_kernel<<<blocks_for((int64_t)B * K), 256, 0, st>>>((int64_t)B * K, s->dXf,
-                                                                         s->Z[l - 1], s->dZf, s->dZb);
+        silu_backward_kernel<<<blocks_for((int64_t)B * K), 256, 0, st>>>(B, K, s->dXf, s->Z[l - 1],
+                                                                         s->dZf, s->dZb, s->dZT);
         e = cudaGetLastError();
     }
     return e;
@@ -437,6 +468,16 @@ int check_err(gt_surrogate *s, cudaStream_t st)
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return GT_ERR_CUDA;
     return h ? GT_ERR_TIMEOUT : GT_OK;
+}
+
+// bf16 copies of the parameters and transposed bf16 weights after an update
+cudaError_t refresh_bf16(gt_surrogate *s, cudaStream_t st)
+{
+    to_bf16_kernel<<<blocks_for(s->n_params), 256, 0, st>>>(s->n_params, s->p, s->wb);
+    for (int l = 0; l < N_LAYERS; l++)
+        weights_t_kernel<<<blocks_for((int64_t)OUT_DIM[l] * IN_DIM[l]), 256, 0, st>>>(
+            s->p + s->w_off[l], OUT_DIM[l], IN_DIM[l], s->WT + s->w_off[l]);
+    return cudaGetLastError();
 }
 
 } // namespace
@@ -500,6 +541,7 @@ int gt_surrogate_create(int device, const gt_surrogate_norm *nrm, uint64_t seed,
     if (e == cudaSuccess) e = cudaMalloc(&s->m, off * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&s->v, off * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&s->wb, off * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMalloc(&s->WT, off * sizeof(__nv_bfloat16));
     if (e == cudaSuccess) e = cudaMalloc(&s->decay, off);
     if (e == cudaSuccess) e = cudaMalloc(&s->loss, sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&s->err, sizeof(int));
@@ -515,8 +557,8 @@ int gt_surrogate_create(int device, const gt_surrogate_norm *nrm, uint64_t seed,
     if (e == cudaSuccess) e = cudaMemset(s->err, 0, sizeof(int));
     if (e == cudaSuccess) {
         init_params_kernel<<<blocks_for(off), 256>>>(s->p, off, d_offs, d_scales, (int)offs.size(), seed);
-        to_bf16_kernel<<<blocks_for(off), 256>>>(off, s->p, s->wb);
-        e = cudaDeviceSynchronize();
+        e = refresh_bf16(s, 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
     }
     cudaFree(d_offs);
     cudaFree(d_scales);
@@ -539,6 +581,7 @@ int gt_surrogate_destroy(gt_surrogate *s)
     cudaFree(s->m);
     cudaFree(s->v);
     cudaFree(s->wb);
+    cudaFree(s->WT);
     cudaFree(s->decay);
     cudaFree(s->loss);
     cudaFree(s->err);
@@ -559,10 +602,8 @@ int gt_surrogate_set_params(gt_surrogate *s, const float *host, int64_t n)
     if (!s || !host || n != s->n_params) return GT_ERR_INVALID_ARG;
     Dev d(s->device);
     cudaError_t e = cudaMemcpy(s->p, host, n * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) {
-        to_bf16_kernel<<<blocks_for(n), 256>>>(n, s->p, s->wb);
-        e = cudaDeviceSynchronize();
-    }
+    if (e == cudaSuccess) e = refresh_bf16(s, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     return e == cudaSuccess ? GT_OK : GT_ERR_CUDA;
 }
 
@@ -600,7 +641,8 @@ int gt_surrogate_grad(gt_ctx *ctx, gt_surrogate *s, int64_t n, const double *alp
     cudaStream_t st = gt_internal_stream(ctx);
     int rc = ensure_ws(s, n);
     if (rc != GT_OK) return rc;
-    features_kernel<<<blocks_for(n), 256, 0, st>>>(n, 0, alpha, beta, spin, q, theta0, s->norm, s->X[0]);
+    features_kernel<<<blocks_for(n), 256, 0, st>>>(n, 0, alpha, beta, spin, q, theta0, s->norm, s->X[0],
+                                                   s->XT[0]);
     labels_kernel<<<blocks_for(n), 256, 0, st>>>(n, 0, status, th_end, ph_end, s->lab);
     cudaError_t e = cudaMemsetAsync(s->loss, 0, sizeof(float), st);
     if (e == cudaSuccess) e = forward(s, (int)n, st);
@@ -637,7 +679,7 @@ int gt_surrogate_train(gt_ctx *ctx, gt_surrogate *s, const gt_train_cfg *cfg, in
             const double prog = ((double)ep * nb + b) / ((double)cfg->epochs * nb);
             const float lr = (float)(cfg->lr * 0.5 * (1.0 + cos(M_PI * prog)));
             features_kernel<<<blocks_for(B), 256, 0, st>>>(B, b * B, alpha, beta, spin, q, theta0,
-                                                           s->norm, s->X[0]);
+                                                           s->norm, s->X[0], s->XT[0]);
             labels_kernel<<<blocks_for(B), 256, 0, st>>>(B, b * B, status, th_end, ph_end, s->lab);
             e = forward(s, B, st);
             if (e == cudaSuccess) e = backward(s, B, (float)cfg->dir_weight, st);
@@ -648,8 +690,7 @@ int gt_surrogate_train(gt_ctx *ctx, gt_surrogate *s, const gt_train_cfg *cfg, in
                                                                   lr, b1, b2, eps,
                                                                   (float)cfg->weight_decay, bc1, bc2,
                                                                   s->decay);
-            to_bf16_kernel<<<blocks_for(s->n_params), 256, 0, st>>>(s->n_params, s->p, s->wb);
-            e = cudaGetLastError();
+            e = refresh_bf16(s, st);
         }
         if (e != cudaSuccess) return GT_ERR_CUDA;
         if (loss_per_epoch) {

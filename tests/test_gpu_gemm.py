@@ -65,3 +65,16 @@ def test_gemm_transposed_views_and_split_k(lib):
     C = gemm(lib, At, Bt, M, N, K, (1, M), (1, N), splits=5, bn=32)
     R = ref(At.t().contiguous(), Bt.t().contiguous())
     np.testing.assert_allclose(C.cpu().numpy(), R, rtol=1e-4, atol=1e-4 * np.sqrt(K))
+
+
+def test_gemm_pipeline_long_k_ragged_edges(lib):
+    """K-contiguous operands take the multi-stage cp.async pipeline: many chunks (stage
+    reuse), a K tail that is not a multiple of the chunk, ragged M and N."""
+    M, N, K = 301, 200, 1000 + 8
+    g = torch.Generator().manual_seed(5)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16).cuda()
+    B = torch.randn(N, K, generator=g).to(torch.bfloat16).cuda()
+    for bn, splits in ((256, 1), (64, 3)):
+        C = gemm(lib, A, B, M, N, K, (K, 1), (K, 1), splits=splits, bn=bn)
+        R = ref(A, B)
+        np.testing.assert_allclose(C.cpu().numpy(), R, rtol=1e-4, atol=1e-4 * np.sqrt(K))

@@ -1,7 +1,9 @@
 """FP64 CPU reference of the surrogate network -- TEST INFRASTRUCTURE ONLY.
 
 Plain numpy forward and backward pass of the MLP the CUDA library trains:
-features (alpha, beta, a/M, q, theta0) normalised to about [-1, 1], zero padded to 16,
+inputs (alpha, beta, a/M, q, theta0) normalised to about [-1, 1], plus the polar form
+(rho, cos psi, sin psi) of the scaled pixel direction and (cos, sin) of theta0, zero
+padded to 16 columns,
 layers 16 -> 256 -> 256 -> 256 -> 256 -> 16 with SiLU between them, output
 (escape logit, end-direction vector, 12 unused), loss
     mean( BCE(logit, y) + w * y * |d_pred - d|^2 ),
@@ -50,11 +52,20 @@ def features(alpha, beta, spin, q, theta0, r0=15.0, fov_deg=75.0, spin_max=0.99,
     V = math.tan(0.5 * fov_deg / 180 * math.pi) / r0
     H = math.atan(math.tan(V))
     X = np.zeros((len(alpha), 16))
-    X[:, 0] = np.asarray(alpha) / H
-    X[:, 1] = np.asarray(beta) / V
+    a = np.asarray(alpha, dtype=np.float64) / H
+    b = np.asarray(beta, dtype=np.float64) / V
+    th = np.asarray(theta0, dtype=np.float64)
+    X[:, 0] = a
+    X[:, 1] = b
     X[:, 2] = np.asarray(spin) * (2 / spin_max) - 1
     X[:, 3] = np.asarray(q) / q_max
-    X[:, 4] = np.asarray(theta0) * (2 / (th_max - th_min)) - (th_max + th_min) / (th_max - th_min)
+    X[:, 4] = th * (2 / (th_max - th_min)) - (th_max + th_min) / (th_max - th_min)
+    rho = np.hypot(a, b)
+    X[:, 5] = rho
+    X[:, 6] = a / np.maximum(rho, 1e-3)   # cos psi
+    X[:, 7] = b / np.maximum(rho, 1e-3)   # sin psi
+    X[:, 8] = np.cos(th)
+    X[:, 9] = np.sin(th)
     return X
 
 
@@ -121,6 +132,6 @@ def init_params(seed=0):
     p = np.zeros(n_params())
     ws, _ = split(p)
     for l, w in enumerate(ws):
-        fan = 5 if l == 0 else IN[l]
+        fan = 10 if l == 0 else IN[l]
         w[...] = rng.normal(0, 1 / math.sqrt(fan), w.shape)
     return p

@@ -3,7 +3,8 @@
 // produces, evaluated with the tcgen05 BF16 GEMM, and backed by the integrator for
 // low-confidence and photon-ring pixels.
 //
-// Network: 16 (5 features, zero padded) -> 256 -> 256 -> 256 -> 256 -> 16 (4 used:
+// Network: 16 (5 inputs and 5 columns derived from them, zero padded) -> 256 -> 256 ->
+// 256 -> 256 -> 16 (4 used:
 // logit and the unit vector of the end direction, which unlike (theta, phi) has no
 // jump at phi = +-pi), SiLU between layers.  FP32 master weights and AdamW state;
 // BF16 weights and activations feed the tensor cores; accumulation is FP32.
@@ -56,6 +57,30 @@ __global__ void init_params_kernel(float *p, int64_t n, const int64_t *offs, con
     p[i] = sc * (float)(sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2));
 }
 
+// The network's 16 input columns from the 5 inputs (alpha, beta, a/M, q, theta0):
+// 0-4 the inputs scaled to about [-1, 1]; 5-7 the pixel direction in polar form
+// (rho, cos psi, sin psi) of the scaled (alpha, beta); 8-9 cos and sin of theta0; the
+// rest zero.  The derived columns are fixed functions of the inputs.
+__device__ __forceinline__ void make_features(double al, double bt, double spin, double q,
+                                              double th0, const Norm &nm, float f[16])
+{
+    const double a = al * nm.inv_h, b = bt * nm.inv_v;
+    const double rho = sqrt(a * a + b * b);
+    const double irho = 1.0 / fmax(rho, 1e-3);
+    f[0] = (float)a;
+    f[1] = (float)b;
+    f[2] = (float)(spin * nm.spin_scale + nm.spin_shift);
+    f[3] = (float)(q * nm.q_scale);
+    f[4] = (float)(th0 * nm.th_scale + nm.th_shift);
+    f[5] = (float)rho;
+    f[6] = (float)(a * irho);
+    f[7] = (float)(b * irho);
+    f[8] = (float)cos(th0);
+    f[9] = (float)sin(th0);
+#pragma unroll
+    for (int j = 10; j < 16; j++) f[j] = 0.0f;
+}
+
 // features of samples [row0, row0 + n): X0[r, 0..15] (bf16)
 __global__ void features_kernel(int64_t n, int64_t row0, const double *alpha, const double *beta,
                                 const double *spin, const double *q, const double *theta0,
@@ -65,13 +90,7 @@ __global__ void features_kernel(int64_t n, int64_t row0, const double *alpha, co
     if (r >= n) return;
     const int64_t k = row0 + r;
     float f[16];
-    f[0] = (float)(alpha[k] * nm.inv_h);
-    f[1] = (float)(beta[k] * nm.inv_v);
-    f[2] = (float)(spin[k] * nm.spin_scale + nm.spin_shift);
-    f[3] = (float)(q[k] * nm.q_scale);
-    f[4] = (float)(theta0[k] * nm.th_scale + nm.th_shift);
-#pragma unroll
-    for (int j = 5; j < 16; j++) f[j] = 0.0f;
+    make_features(alpha[k], beta[k], spin[k], q[k], theta0[k], nm, f);
 #pragma unroll
     for (int j = 0; j < 16; j++) X0[r * 16 + j] = __float2bfloat16(f[j]);
     if (X0T)
@@ -91,13 +110,7 @@ __global__ void camera_features_kernel(int64_t n, int64_t pix0, const CamDesc *c
     const double al = c.res_x > 1 ? c.H * (double)(2 * i - (c.res_x - 1)) / (double)(c.res_x - 1) : 0.0;
     const double bt = c.res_y > 1 ? c.V * (double)(2 * j - (c.res_y - 1)) / (double)(c.res_y - 1) : 0.0;
     float f[16];
-    f[0] = (float)(al * nm.inv_h);
-    f[1] = (float)(bt * nm.inv_v);
-    f[2] = (float)((c.S / c.M) / c.M * nm.spin_scale + nm.spin_shift);
-    f[3] = (float)(c.Q * nm.q_scale);
-    f[4] = (float)(c.th0 * nm.th_scale + nm.th_shift);
-#pragma unroll
-    for (int jj = 5; jj < 16; jj++) f[jj] = 0.0f;
+    make_features(al, bt, (c.S / c.M) / c.M, c.Q, c.th0, nm, f);
 #pragma unroll
     for (int jj = 0; jj < 16; jj++) X0[r * 16 + jj] = __float2bfloat16(f[jj]);
 }
@@ -521,8 +534,8 @@ int gt_surrogate_create(int device, const gt_surrogate_norm *nrm, uint64_t seed,
     for (int l = 0; l < N_LAYERS; l++) {
         s->w_off[l] = off;
         offs.push_back(off);
-        // LeCun-normal weights (the 11 zero-padded input features do not count)
-        const int fan_in = l == 0 ? 5 : IN_DIM[l];
+        // LeCun-normal weights (the 6 zero-padded input columns do not count)
+        const int fan_in = l == 0 ? 10 : IN_DIM[l];
         scales.push_back((float)(1.0 / sqrt((double)fan_in)));
         off += (int64_t)OUT_DIM[l] * IN_DIM[l];
         s->b_off[l] = off;

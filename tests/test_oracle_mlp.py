@@ -24,7 +24,7 @@ def test_fp64_gradient_matches_finite_differences():
     ws, bs = mlp.split(np.arange(p.size))
     idx = []
     for w, b in zip(ws, bs):
-        idx += list(rng.choice(w.ravel()[np.nonzero(w.ravel() % 16 < 5)[0]] if w.shape[1] == 16
+        idx += list(rng.choice(w.ravel()[np.nonzero(w.ravel() % 16 < 10)[0]] if w.shape[1] == 16
                                else w.ravel(), 4, replace=False)) + list(rng.choice(b, 2))
     for i in idx:
         h = 1e-6
@@ -48,3 +48,7 @@ def test_features_cover_unit_range():
                      [5 * np.pi / 180, np.pi / 2])
     assert np.allclose(X[:, 2], [-1, 1]) and np.allclose(X[:, 4], [-1, 1])
     assert np.all(np.abs(X[:, :2]) < 1.01)
+    # polar columns: rho and a unit (cos psi, sin psi); cos/sin of theta0
+    assert np.allclose(X[:, 5], np.hypot(X[:, 0], X[:, 1]))
+    assert np.allclose(X[:, 6] ** 2 + X[:, 7] ** 2, 1.0)
+    assert np.allclose(X[:, 8] ** 2 + X[:, 9] ** 2, 1.0) and np.all(X[:, 10:] == 0)

@@ -325,8 +325,8 @@ def leg_gemm(geotrace, args, torch):
     peak = peaks.get("bf16_tflops", 1900.0)
     res = {"peak_tflops": peak, "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)"}
     g = torch.Generator(device="cuda").manual_seed(1)
-    for name, (M, N, K, splits, bn) in {"forward_hidden": (1 << 20, 256, 256, 1, 256),
-                                        "weight_grad": (256, 256, 1 << 16, 128, 256)}.items():
+    for name, (M, N, K, splits, bn) in {"forward_hidden": (1 << 20, 256, 256, 1, 128),
+                                        "weight_grad": (256, 256, 1 << 16, 128, 128)}.items():
         A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
         B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
         C = torch.zeros(M, N, device="cuda", dtype=torch.float32)

@@ -48,7 +48,8 @@ def _stale() -> bool:
 
 def _compile(src: str) -> tuple:
     obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-    cmd = [nvcc()] + ARCH + FLAGS + ["-c", src, "-o", obj]
+    extra = os.environ.get("GT_NVCC_EXTRA", "").split()  # e.g. -DGT_FIELD_NOINLINE
+    cmd = [nvcc()] + ARCH + FLAGS + extra + ["-c", src, "-o", obj]
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, p.stdout, p.stderr))

@@ -78,6 +78,58 @@ __device__ __forceinline__ void stage_tile(uint8_t *sm, const __nv_bfloat16 *__r
 
 __device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
 
+
+// Epilogue shared by both kernels: TMEM -> registers (thread = row) -> bias -> shared
+// memory tile (32 columns at a time) -> coalesced stores where each warp writes
+// 32 consecutive columns of one row.  The transposed bf16 copy is written straight from
+// the row owner (consecutive lanes = consecutive rows, already coalesced).
+__device__ __forceinline__ void gemm_epilogue(const GemmArgs &g, uint32_t tmem, int BN_, int m0,
+                                              int n0, bool have_acc, float *stage /* 128 x 33 */)
+{
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row_own = m0 + warp * 32 + lane;
+    for (int cc = 0; cc < BN_; cc += 32) {
+        float v[32];
+        if (have_acc) {
+            tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc, v);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 32; i++) v[i] = 0.0f;
+        }
+#pragma unroll
+        for (int i = 0; i < 32; i++) {
+            const int col = n0 + cc + i;
+            float z = v[i];
+            if (g.bias && blockIdx.z == 0 && col < g.N) z += g.bias[col];
+            stage[(warp * 32 + lane) * 33 + i] = z;
+            if (g.C16T && row_own < g.M && col < g.N)
+                g.C16T[(int64_t)col * g.ldt + row_own] =
+                    __float2bfloat16(g.act == 1 ? silu(z) : z);
+        }
+        __syncthreads();
+        // 128 rows x 32 columns: warp w writes rows w, w + 4, ..., lane = column
+        const int col = n0 + cc + lane;
+        if (col < g.N && cc + lane < BN_) {
+            for (int rr = warp; rr < 128; rr += 4) {
+                const int row = m0 + rr;
+                if (row >= g.M) break;
+                const float z = stage[rr * 33 + lane];
+                if (g.pre) g.pre[(int64_t)row * g.ld_pre + col] = z;
+                const float y = g.act == 1 ? silu(z) : z;
+                if (g.C32) {
+                    float *p = g.C32 + (int64_t)row * g.ldc + col;
+                    if (g.atomic)
+                        atomicAdd(p, y);
+                    else
+                        *p = y;
+                }
+                if (g.C16) g.C16[(int64_t)row * g.ldc16 + col] = __float2bfloat16(y);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 template <int BN>
 __global__ void __launch_bounds__(128) tc_gemm_kernel(GemmArgs g)
 {
@@ -111,20 +163,22 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(GemmArgs g)
     const bool b_vec = (g.b_sk == 1) && (g.b_sn % 8 == 0) && ((uintptr_t)g.B % 16 == 0);
     constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
 
-    for (int c = 0; c < nk && ok; ++c) {
+    for (int c = 0; c < nk; ++c) {
         const int s = c & 1;
         if (c >= 2) {
             ok = tc::mbar_wait(tc::smem_u32(&mbar[s]), (uint32_t)(((c - 2) >> 1) & 1), WAIT_LIMIT);
-            if (!ok) break;
             tc::fence_after_sync();
         }
         uint8_t *As = smem + s * L::STAGE;
         uint8_t *Bs = As + L::A_BYTES;
         const int k0 = (c_begin + c) * BK;
-        stage_tile(As, g.A, g.M, g.K, g.a_sm, g.a_sk, m0, k0, BM, L::A_LBO, a_vec);
-        stage_tile(Bs, g.B, g.N, g.K, g.b_sn, g.b_sk, n0, k0, BN, L::B_LBO, b_vec);
+        if (ok) {
+            stage_tile(As, g.A, g.M, g.K, g.a_sm, g.a_sk, m0, k0, BM, L::A_LBO, a_vec);
+            stage_tile(Bs, g.B, g.N, g.K, g.b_sn, g.b_sk, n0, k0, BN, L::B_LBO, b_vec);
+        }
         tc::fence_proxy_async();
-        __syncthreads();
+        ok = __syncthreads_and(ok ? 1 : 0) != 0; // uniform: every thread leaves together
+        if (!ok) break;
         if (tid == 0) {
             tc::fence_after_sync();
             const uint32_t a_base = tc::smem_u32(As), b_base = tc::smem_u32(Bs);
@@ -141,41 +195,13 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(GemmArgs g)
         const int last = nk - 1;
         ok = tc::mbar_wait(tc::smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1), WAIT_LIMIT);
     }
-    __syncthreads(); // every thread knows the outcome through its own wait
+    ok = __syncthreads_and(ok ? 1 : 0) != 0; // one outcome for the whole CTA
     tc::fence_after_sync();
     if (!ok) {
         if (tid == 0 && g.err) atomicExch(g.err, 1);
     } else {
-        const int row = m0 + warp * 32 + lane;
-        for (int cc = 0; cc < BN; cc += 32) {
-            float v[32];
-            if (nk > 0) {
-                tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc, v);
-            } else {
-#pragma unroll
-                for (int i = 0; i < 32; i++) v[i] = 0.0f;
-            }
-            if (row < g.M) {
-#pragma unroll
-                for (int i = 0; i < 32; i++) {
-                    const int col = n0 + cc + i;
-                    if (cc + i >= BN || col >= g.N) continue;
-                    float z = v[i];
-                    if (g.bias && blockIdx.z == 0) z += g.bias[col];
-                    if (g.pre) g.pre[(int64_t)row * g.ld_pre + col] = z;
-                    const float y = g.act == 1 ? silu(z) : z;
-                    if (g.C32) {
-                        float *p = g.C32 + (int64_t)row * g.ldc + col;
-                        if (g.atomic)
-                            atomicAdd(p, y);
-                        else
-                            *p = y;
-                    }
-                    if (g.C16) g.C16[(int64_t)row * g.ldc16 + col] = __float2bfloat16(y);
-                    if (g.C16T) g.C16T[(int64_t)col * g.ldt + row] = __float2bfloat16(y);
-                }
-            }
-        }
+        // the operand stages are free now: reuse them as the epilogue's staging tile
+        gemm_epilogue(g, tmem, BN, m0, n0, nk > 0, reinterpret_cast<float *>(smem));
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -259,7 +285,8 @@ __global__ void __launch_bounds__(128) tc_gemm_pipe_kernel(GemmArgs g)
     for (int c = 0; c < nk; ++c) {
         cp_async_wait<STAGES - 2>(); // this thread's pieces of chunk c have landed
         tc::fence_proxy_async();
-        __syncthreads();
+        ok = __syncthreads_and(ok ? 1 : 0) != 0; // uniform: every thread leaves together
+        if (!ok) break;
         if (tid == 0) {
             tc::fence_after_sync();
             const uint32_t a_base = sbase + (c % STAGES) * L::STAGE, b_base = a_base + L::A_BYTES;
@@ -275,9 +302,8 @@ __global__ void __launch_bounds__(128) tc_gemm_pipe_kernel(GemmArgs g)
         if (c >= 1 && nc < nk) { // chunk nc reuses the stage of chunk c - 1
             ok = tc::mbar_wait(tc::smem_u32(&mbar[(c - 1) % STAGES]),
                                (uint32_t)(((c - 1) / STAGES) & 1), WAIT_LIMIT);
-            if (!ok) break;
         }
-        if (nc < nk) issue(nc);
+        if (ok && nc < nk) issue(nc);
         cp_async_commit();
     }
     cp_async_wait<0>();
@@ -286,41 +312,13 @@ __global__ void __launch_bounds__(128) tc_gemm_pipe_kernel(GemmArgs g)
         ok = tc::mbar_wait(tc::smem_u32(&mbar[last % STAGES]), (uint32_t)((last / STAGES) & 1),
                            WAIT_LIMIT);
     }
-    __syncthreads();
+    ok = __syncthreads_and(ok ? 1 : 0) != 0; // one outcome for the whole CTA
     tc::fence_after_sync();
     if (!ok) {
         if (tid == 0 && g.err) atomicExch(g.err, 1);
     } else {
-        const int row = m0 + warp * 32 + lane;
-        for (int cc = 0; cc < BN; cc += 32) {
-            float v[32];
-            if (nk > 0) {
-                tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc, v);
-            } else {
-#pragma unroll
-                for (int i = 0; i < 32; i++) v[i] = 0.0f;
-            }
-            if (row < g.M) {
-#pragma unroll
-                for (int i = 0; i < 32; i++) {
-                    const int col = n0 + cc + i;
-                    if (cc + i >= BN || col >= g.N) continue;
-                    float z = v[i];
-                    if (g.bias && blockIdx.z == 0) z += g.bias[col];
-                    if (g.pre) g.pre[(int64_t)row * g.ld_pre + col] = z;
-                    const float y = g.act == 1 ? silu(z) : z;
-                    if (g.C32) {
-                        float *p = g.C32 + (int64_t)row * g.ldc + col;
-                        if (g.atomic)
-                            atomicAdd(p, y);
-                        else
-                            *p = y;
-                    }
-                    if (g.C16) g.C16[(int64_t)row * g.ldc16 + col] = __float2bfloat16(y);
-                    if (g.C16T) g.C16T[(int64_t)col * g.ldt + row] = __float2bfloat16(y);
-                }
-            }
-        }
+        // the operand stages are free now: reuse them as the epilogue's staging tile
+        gemm_epilogue(g, tmem, BN, m0, n0, nk > 0, reinterpret_cast<float *>(smem));
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -331,7 +329,7 @@ template <int BN>
 cudaError_t launch_pipe(const GemmArgs &g, int splits, cudaStream_t s)
 {
     using L = GemmSmem<BN>;
-    constexpr int STAGES = 4;
+    constexpr int STAGES = 3;
     const uint32_t bytes = STAGES * L::STAGE + 8 * STAGES + 64;
     cudaError_t e = cudaFuncSetAttribute(tc_gemm_pipe_kernel<BN, STAGES>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);

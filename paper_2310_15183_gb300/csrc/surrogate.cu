@@ -426,7 +426,8 @@ cudaError_t gemm(const __nv_bfloat16 *A, int64_t a_sm, int64_t a_sk, const __nv_
     g.C16T = C16T;
     g.ldt = M;
     g.err = err;
-    const int bn = N >= 256 ? 256 : (N >= 128 ? 128 : (N >= 64 ? 64 : (N >= 32 ? 32 : 16)));
+    // 128-wide tiles: two CTAs fit per SM (3 stages x 32 KB of operands each)
+    const int bn = N >= 128 ? 128 : (N >= 64 ? 64 : (N >= 32 ? 32 : 16));
     return launch_gemm(g, bn, splits, st);
 }
 

@@ -325,7 +325,10 @@ def leg_gemm(geotrace, args, torch):
     peak = peaks.get("bf16_tflops", 1900.0)
     res = {"peak_tflops": peak, "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)"}
     g = torch.Generator(device="cuda").manual_seed(1)
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    res["peak_hbm_gbs"] = hbm
     for name, (M, N, K, splits, bn) in {"forward_hidden": (1 << 20, 256, 256, 1, 128),
+                                        "forward_hidden_bn256": (1 << 20, 256, 256, 1, 256),
                                         "weight_grad": (256, 256, 1 << 16, 128, 128)}.items():
         A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
         B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
@@ -354,8 +357,12 @@ def leg_gemm(geotrace, args, torch):
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) / 1e3 / reps
         tf = 2.0 * M * N * K / t / 1e12
-        res[name] = {"M": M, "N": N, "K": K, "splits": splits, "seconds": t, "tflops": tf,
-                     "frac_of_peak": tf / peak}
+        # algorithmic bytes: both operands read once, the FP32 result written once
+        # (read as well when split-K accumulates into it)
+        nbytes = 2 * (M * K + N * K) + 4 * M * N * (2 if splits > 1 else 1)
+        res[name] = {"M": M, "N": N, "K": K, "splits": splits, "bn": bn, "seconds": t,
+                     "tflops": tf, "frac_of_peak": tf / peak, "bytes": nbytes,
+                     "gbs": nbytes / t / 1e9, "frac_of_hbm": nbytes / t / 1e9 / hbm}
     return res
 
 

@@ -9,9 +9,14 @@
 //   loads when K is contiguous), one thread issues four 128 x BN x 16 MMAs and
 //   commits them to the stage's mbarrier, which the stage's next writer waits on.
 //   Split-K over gridDim.z accumulates into C with atomics.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 #include <stdint.h>
+
+#include <mutex>
+#include <stdlib.h>
 
 #include "../../include/geotrace.h"
 #include "mlp.cuh"
@@ -339,6 +344,262 @@ cudaError_t launch_pipe(const GemmArgs &g, int splits, cudaStream_t s)
     return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------------
+// Persistent warp-specialised variant (K-contiguous operands with TMA tensor maps).
+// 320 threads: warp 0 lane 0 loads A and B chunks with 2-D TMA boxes of 8 elements x
+// (128 | BN) rows -- exactly one K-column of core matrices each -- into S stages;
+// warp 1 lane 0 issues the MMAs into one of two TMEM accumulators; warps 2-9 drain the
+// other accumulator (bias, SiLU, stores) meanwhile, two warps per TMEM lane quarter
+// taking alternate 32-column chunks.  Stage and accumulator hand-offs are
+// mbarriers (TMA complete_tx, tcgen05.commit, epilogue arrivals); every wait is bounded.
+constexpr int EPI_WARPS = 8;
+constexpr int WS_THREADS = 64 + 32 * EPI_WARPS;
+
+template <int BN, int S>
+struct WsSmem {
+    static constexpr uint32_t A_BYTES = BM * BK * 2;
+    static constexpr uint32_t B_BYTES = BN * BK * 2;
+    static constexpr uint32_t STAGE = A_BYTES + B_BYTES;
+    static constexpr uint32_t EPI = EPI_WARPS * 32 * 33 * 4; // per-warp 32 x 33 float staging
+    static constexpr uint32_t BAR = S * STAGE + EPI;
+    static constexpr uint32_t NBAR = 2 * S + 5; // full[S], empty[S], acc_full[2], acc_empty[2], done
+    static constexpr uint32_t TOTAL = BAR + 8 * NBAR + 16;
+    static constexpr uint32_t A_LBO = (BM / 8) * 128;
+    static constexpr uint32_t B_LBO = (BN / 8) * 128;
+    static constexpr uint32_t NCOLS = 2 * BN < 32 ? 32 : 2 * BN; // two accumulators    static_assert(TOTAL <= 227 * 1024, "shared memory per CTA");
+};
+
+template <int BN, int S>
+__global__ void __launch_bounds__(WS_THREADS, 1)
+    tc_gemm_ws_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                      GemmArgs g, int splits)
+{
+    using L = WsSmem<BN, S>;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    const uint32_t sbase = tc::smem_u32(smem);
+    const uint32_t bar = sbase + L::BAR;
+    auto FULL = [&](int s) { return bar + 8u * s; };
+    auto EMPTY = [&](int s) { return bar + 8u * (S + s); };
+    auto ACCF = [&](int b) { return bar + 8u * (2 * S + b); };
+    auto ACCE = [&](int b) { return bar + 8u * (2 * S + 2 + b); };
+    const uint32_t DONE = bar + 8u * (2 * S + 4);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::BAR + 8 * L::NBAR);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    const int m_tiles = (g.M + BM - 1) / BM, n_tiles = (g.N + BN - 1) / BN;
+    const int nk_total = (g.K + BK - 1) / BK;
+    const int per = (nk_total + splits - 1) / splits;
+    const int total = m_tiles * n_tiles * splits;
+
+    if (warp == 1) tc::tmem_alloc(tc::smem_u32(tmem_slot), L::NCOLS);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; s++) {
+            tc::mbar_init(FULL(s), 1);
+            tc::mbar_init(EMPTY(s), 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            tc::mbar_init(ACCF(b), 1);
+            tc::mbar_init(ACCE(b), EPI_WARPS);
+        }
+        tc::mbar_init(DONE, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    bool ok = true;
+
+    if (warp == 0) {
+        if (lane == 0) { // ---- producer
+            uint32_t q = 0;
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+                const int mt = t % m_tiles, nt = (t / m_tiles) % n_tiles, ks = t / (m_tiles * n_tiles);
+                const int c0 = ks * per, c1 = min(nk_total, c0 + per);
+                for (int c = c0; c < c1; ++c, ++q) {
+                    const int s = q % S;
+                    if (q >= (uint32_t)S) {
+                        ok = tc::mbar_wait(EMPTY(s), ((q / S) - 1) & 1, WAIT_LIMIT);
+                        if (!ok) break;
+                    }
+                    tc::mbar_expect_tx(FULL(s), L::STAGE);
+                    const uint32_t a_dst = sbase + s * L::STAGE, b_dst = a_dst + L::A_BYTES;
+#pragma unroll
+                    for (int kb = 0; kb < BK / 8; kb++) {
+                        tc::tma_load_2d(a_dst + kb * L::A_LBO, &tmA, c * BK + kb * 8, mt * BM, FULL(s));
+                        tc::tma_load_2d(b_dst + kb * L::B_LBO, &tmB, c * BK + kb * 8, nt * BN, FULL(s));
+                    }
+                }
+            }
+            // copies still in flight (only after a failed wait) land before the CTA exits
+            for (uint32_t j = q > (uint32_t)S ? q - S : 0; j < q; ++j)
+                if (!tc::mbar_wait(FULL(j % S), (j / S) & 1, WAIT_LIMIT)) ok = false;
+        }
+    } else if (warp == 1) {
+        if (lane == 0) { // ---- MMA issuer
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+            uint32_t q = 0, tl = 0;
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++tl) {
+                const int ks = t / (m_tiles * n_tiles);
+                const int c0 = ks * per, c1 = min(nk_total, c0 + per);
+                const int b = tl & 1;
+                if (tl >= 2) {
+                    ok = tc::mbar_wait(ACCE(b), ((tl >> 1) - 1) & 1, WAIT_LIMIT);
+                    if (!ok) break;
+                }
+                tc::fence_after_sync();
+                const uint32_t d = tmem + (uint32_t)(b * BN);
+                for (int c = c0; c < c1; ++c, ++q) {
+                    const int s = q % S;
+                    ok = tc::mbar_wait(FULL(s), (q / S) & 1, WAIT_LIMIT);
+                    if (!ok) break;
+                    tc::fence_after_sync();
+                    const uint32_t a_base = sbase + s * L::STAGE, b_base = a_base + L::A_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        const uint64_t ad = tc::smem_desc(a_base + kk * 2 * L::A_LBO, L::A_LBO, 128);
+                        const uint64_t bd = tc::smem_desc(b_base + kk * 2 * L::B_LBO, L::B_LBO, 128);
+                        tc::mma_bf16(d, ad, bd, idesc, (c > c0 || kk > 0) ? 1u : 0u);
+                    }
+                    tc::mma_commit(EMPTY(s));
+                }
+                if (!ok) break;
+                tc::mma_commit(ACCF(b));
+            }
+            // every issued MMA completes before the accumulators are freed
+            tc::mma_commit(DONE);
+            if (!tc::mbar_wait(DONE, 0, WAIT_LIMIT)) ok = false;
+        }
+    } else { // ---- epilogue warps 2..9: TMEM lanes 32 * (warp % 4), column chunks by half
+        const int quarter = warp & 3, half = (warp - 2) >> 2;
+        float *stg = reinterpret_cast<float *>(smem + S * L::STAGE) + (warp - 2) * 32 * 33;
+        uint32_t tl = 0;
+        for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++tl) {
+            const int mt = t % m_tiles, nt = (t / m_tiles) % n_tiles, ks = t / (m_tiles * n_tiles);
+            const int b = tl & 1;
+            ok = tc::mbar_wait(ACCF(b), (tl >> 1) & 1, WAIT_LIMIT);
+            if (!ok) break;
+            tc::fence_after_sync();
+            const int m0 = mt * BM + quarter * 32, n0 = nt * BN;
+            const int row_own = m0 + lane;
+            for (int cc = 32 * half; cc < BN; cc += 64) {
+                float v[32];
+                tc::tmem_ld32(tmem + (uint32_t)(b * BN + cc) + ((uint32_t)(quarter * 32) << 16), v);
+                // lane owns column n0 + cc + lane in the store phase below
+                const int col = n0 + cc + lane;
+                const bool col_ok = cc + lane < BN && col < g.N;
+                const float bias = (g.bias && ks == 0 && col_ok) ? g.bias[col] : 0.f;
+                if (g.C16T) { // transposed bf16 copy, written by the row owner
+#pragma unroll
+                    for (int i = 0; i < 32; i++) {
+                        const float z = v[i] + __shfl_sync(0xffffffffu, bias, i);
+                        const int c = n0 + cc + i;
+                        if (row_own < g.M && cc + i < BN && c < g.N)
+                            g.C16T[(int64_t)c * g.ldt + row_own] =
+                                __float2bfloat16(g.act == 1 ? silu(z) : z);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 32; i++) stg[lane * 33 + i] = v[i];
+                __syncwarp();
+                if (col_ok) {
+                    const int nrows = min(32, g.M - m0);
+#pragma unroll
+                    for (int rr = 0; rr < 32; rr++) {
+                        if (rr < nrows) {
+                            const int64_t row = m0 + rr;
+                            const float z = stg[rr * 33 + lane] + bias;
+                            if (g.pre) g.pre[row * g.ld_pre + col] = z;
+                            const float y = g.act == 1 ? silu(z) : z;
+                            if (g.C32) {
+                                float *p = g.C32 + row * g.ldc + col;
+                                if (g.atomic)
+                                    atomicAdd(p, y);
+                                else
+                                    *p = y;
+                            }
+                            if (g.C16) g.C16[row * g.ldc16 + col] = __float2bfloat16(y);
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(ACCE(b));
+        }
+    }
+    if (!ok && g.err) atomicExch(g.err, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 1) tc::tmem_dealloc(tmem, L::NCOLS);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
+
+// bf16 matrix of `rows` x `cols` (row stride `ld` elements, K = cols contiguous), boxes of
+// 8 columns x box_rows rows, zero fill outside.
+bool make_map(CUtensorMap *m, const void *base, uint64_t rows, uint64_t cols, uint64_t ld,
+              uint32_t box_rows)
+{
+    auto enc = tensor_map_encoder();
+    if (!enc || rows == 0 || cols == 0 || rows > (1ull << 32) || cols > (1ull << 32)) return false;
+    cuuint64_t dims[2] = {cols, rows};
+    cuuint64_t strides[1] = {ld * 2};
+    cuuint32_t box[2] = {8, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int g_sm_count = 0;
+
+template <int BN>
+cudaError_t launch_ws(const GemmArgs &g, int splits, cudaStream_t s, bool *used)
+{
+    constexpr int S = 4;
+    using L = WsSmem<BN, S>;
+    *used = false;
+    CUtensorMap ta, tb;
+    if (!make_map(&ta, g.A, (uint64_t)g.M, (uint64_t)g.K, (uint64_t)g.a_sm, BM) ||
+        !make_map(&tb, g.B, (uint64_t)g.N, (uint64_t)g.K, (uint64_t)g.b_sn, BN))
+        return cudaSuccess; // caller falls back
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_ws_kernel<BN, S>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, L::TOTAL);
+    if (e != cudaSuccess) return e;
+    if (g_sm_count == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
+    }
+    const int nk_total = (g.K + BK - 1) / BK;
+    if (splits > nk_total) splits = nk_total;
+    splits = (nk_total + ((nk_total + splits - 1) / splits) - 1) / ((nk_total + splits - 1) / splits);
+    const int64_t total = (int64_t)((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN) * splits;
+    const int grid = (int)(total < g_sm_count ? total : g_sm_count);
+    tc_gemm_ws_kernel<BN, S><<<grid, WS_THREADS, L::TOTAL, s>>>(ta, tb, g, splits);
+    *used = true;
+    return cudaGetLastError();
+}
+
 template <int BN>
 cudaError_t launch_bn(const GemmArgs &g, int splits, cudaStream_t s)
 {
@@ -353,11 +614,28 @@ cudaError_t launch_bn(const GemmArgs &g, int splits, cudaStream_t s)
 
 } // namespace
 
+// The warp-specialised TMA kernel is the default for K-contiguous operands; setting
+// GT_GEMM_NO_TMA in the environment selects the cp.async pipeline instead.
+static const bool g_use_ws = getenv("GT_GEMM_NO_TMA") == nullptr;
+
 cudaError_t launch_gemm(const GemmArgs &g, int bn, int splits, cudaStream_t s)
 {
     if (splits < 1) splits = 1;
     const bool pipe = g.a_sk == 1 && g.b_sk == 1 && g.a_sm % 8 == 0 && g.b_sn % 8 == 0 &&
                       ((uintptr_t)g.A % 16) == 0 && ((uintptr_t)g.B % 16) == 0;
+    if (pipe && g.K > 0 && g_use_ws) {
+        bool used = false;
+        cudaError_t e = cudaSuccess;
+        switch (bn) {
+        case 16: e = launch_ws<16>(g, splits, s, &used); break;
+        case 32: e = launch_ws<32>(g, splits, s, &used); break;
+        case 64: e = launch_ws<64>(g, splits, s, &used); break;
+        case 128: e = launch_ws<128>(g, splits, s, &used); break;
+        case 256: e = launch_ws<256>(g, splits, s, &used); break;
+        default: return cudaErrorInvalidValue;
+        }
+        if (e != cudaSuccess || used) return e;
+    }
     if (pipe) {
         switch (bn) {
         case 16: return launch_pipe<16>(g, splits, s);

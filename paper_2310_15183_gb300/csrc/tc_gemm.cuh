@@ -119,3 +119,31 @@ __device__ __forceinline__ uint32_t kmajor_offset(int row, int k, uint32_t lbo)
 
 } // namespace tc
 } // namespace gt
+
+namespace gt {
+namespace tc {
+
+// ---------------------------------------------------------------- TMA and mbarriers
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes)
+                 : "memory");
+}
+// 2-D tiled TMA load of box {x .. x + box0, y .. y + box1} into shared memory; completes
+// on `mbar` with the box's byte count.  x (the innermost coordinate) must keep x * 2
+// bytes a multiple of 16 for bf16 -- callers pass multiples of 8 elements.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void *tmap, int x, int y, uint32_t mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(tmap), "r"(x), "r"(y), "r"(mbar)
+        : "memory");
+}
+
+} // namespace tc
+} // namespace gt

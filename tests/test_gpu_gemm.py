@@ -78,3 +78,31 @@ def test_gemm_pipeline_long_k_ragged_edges(lib):
         C = gemm(lib, A, B, M, N, K, (K, 1), (K, 1), splits=splits, bn=bn)
         R = ref(A, B)
         np.testing.assert_allclose(C.cpu().numpy(), R, rtol=1e-4, atol=1e-4 * np.sqrt(K))
+
+
+@pytest.mark.parametrize("bn", [128, 256])
+def test_gemm_persistent_many_tiles(lib, bn):
+    """More output tiles than SMs: each persistent CTA walks several tiles, so stage
+    phases wrap many times and both TMEM accumulators alternate; ragged M and K."""
+    M, N, K = 51200 + 37, 256, 320 + 24
+    g = torch.Generator().manual_seed(bn)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16).cuda()
+    B = torch.randn(N, K, generator=g).to(torch.bfloat16).cuda()
+    bias = torch.randn(N, generator=g).float().cuda()
+    C = gemm(lib, A, B, M, N, K, (K, 1), (K, 1), bias, 1, bn=bn)
+    R = ref(A, B, bias, 1)
+    np.testing.assert_allclose(C.cpu().numpy(), R, rtol=1e-4, atol=1e-4 * np.sqrt(K))
+
+
+def test_gemm_split_k_uneven(lib):
+    """A split count that does not divide the K chunks (16 chunks over 7 requested
+    splits); every chunk is accumulated exactly once into a pre-filled C."""
+    M, N, K = 200, 64, 1024
+    g = torch.Generator().manual_seed(9)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16).cuda()
+    B = torch.randn(N, K, generator=g).to(torch.bfloat16).cuda()
+    C0 = torch.randn(M, N, generator=g).float()
+    C = gemm(lib, A, B, M, N, K, (K, 1), (K, 1), splits=7, bn=64, accumulate=True,
+             C=C0.clone().cuda())
+    R = ref(A, B) + C0.numpy().astype(np.float64)
+    np.testing.assert_allclose(C.cpu().numpy(), R, rtol=1e-4, atol=1e-4 * np.sqrt(K))

@@ -422,9 +422,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--legs", default="", help="extra legs: batch,surrogate,sweep (comma list)")
     ap.add_argument("--sg-samples", type=int, default=1 << 22)
-    ap.add_argument("--sg-epochs", type=int, default=40)
-    ap.add_argument("--sg-batch", type=int, default=16384)
-    ap.add_argument("--sg-dir-weight", type=float, default=30.0)
+    ap.add_argument("--sg-epochs", type=int, default=120)
+    ap.add_argument("--sg-batch", type=int, default=8192)
+    ap.add_argument("--sg-dir-weight", type=float, default=100.0)
     ap.add_argument("--sg-res", type=int, default=4096)
     ap.add_argument("--batch-scale", type=int, default=8,
                     help="batch leg: camera sides divided by this factor")

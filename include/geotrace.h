@@ -172,9 +172,9 @@ int gt_trace_rays(gt_ctx *ctx, int64_t n, const double *alpha, const double *bet
 
 /* ---------------------------------------------------------------------------------
  * Surrogate: an MLP (alpha, beta, spin a/M, q, theta0) -> (escape logit, unit end
- * direction) with layers 16(5 used) -> 256 -> 256 -> 256 -> 256 -> 16(4 used), SiLU,
- * BF16 weights and activations on tcgen05 tensor cores with FP32 accumulation, FP32
- * master weights and AdamW.  Trained on rays traced by the integrator; the integrator
+ * direction) with layers 16(10 used) -> 256 -> 256 -> 256 -> 256 -> 16(4 used), SiLU,
+ * on tcgen05 tensor cores with FP32 accumulation: FP16 weights and activations in the
+ * forward products, BF16 in the backward products, FP32 master weights and AdamW.  Trained on rays traced by the integrator; the integrator
  * is its fallback.  Not part of the paper's method. */
 typedef struct gt_surrogate gt_surrogate;
 

@@ -8,11 +8,12 @@ layers 16 -> 256 -> 256 -> 256 -> 256 -> 16 with SiLU between them, output
 (escape logit, end-direction vector, 12 unused), loss
     mean( BCE(logit, y) + w * y * |d_pred - d|^2 ),
 where y = 1 for escaped rays and d = (sin th cos ph, sin th sin ph, cos th) of the end
-position.  With `bf16=True` the values are rounded to bfloat16 (round to nearest even) at
-the points where the GPU stores them in bfloat16 (features, hidden activations, weights
-and the gradients fed to the backward products), so that GPU and CPU gradients can be
-compared closely; with `bf16=False` it is the exact FP64 network, whose gradient a
-finite-difference test pins.
+position.  With `bf=True` the values are rounded where the GPU stores them in 16 bits:
+to IEEE half precision for the forward products (layer inputs and weights) and to
+bfloat16 for the backward products (the transposed layer inputs of the weight gradient,
+the weights of the input gradient and the gradients themselves), both round to nearest
+even, so that GPU and CPU gradients can be compared closely; with `bf=False` it is the
+exact FP64 network, whose gradient a finite-difference test pins.
 """
 from __future__ import annotations
 
@@ -45,6 +46,11 @@ def bf16(x) -> np.ndarray:
     u = f.view(np.uint32).astype(np.uint64)
     u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def f16(x) -> np.ndarray:
+    """Round to IEEE binary16 (nearest even); returned as float64."""
+    return np.asarray(x, dtype=np.float64).astype(np.float16).astype(np.float64)
 
 
 def features(alpha, beta, spin, q, theta0, r0=15.0, fov_deg=75.0, spin_max=0.99, q_max=2.0,
@@ -85,22 +91,23 @@ def dsilu(z):
 
 
 def forward(params, X0, bf=True):
-    """Returns the layer inputs X[0..4] and pre-activations Z[0..4]."""
-    r = bf16 if bf else (lambda a: np.asarray(a, dtype=np.float64))
+    """Returns the unrounded layer inputs A[0..4] and the pre-activations Z[0..4]; with
+    bf=True each product takes half-precision inputs and weights."""
+    h = f16 if bf else (lambda a: np.asarray(a, dtype=np.float64))
     ws, bs = split(params)
-    Xs, Zs = [r(X0)], []
+    As, Zs = [np.asarray(X0, dtype=np.float64)], []
     for l in range(5):
-        Z = Xs[-1] @ r(ws[l]).T + bs[l]
+        Z = h(As[-1]) @ h(ws[l]).T + bs[l]
         Zs.append(Z)
         if l < 4:
-            Xs.append(r(silu(Z)))
-    return Xs, Zs
+            As.append(silu(Z))
+    return As, Zs
 
 
 def loss_and_grad(params, X0, y, d, w_dir, bf=True):
     r = bf16 if bf else (lambda a: np.asarray(a, dtype=np.float64))
     ws, _ = split(params)
-    Xs, Zs = forward(params, X0, bf)
+    As, Zs = forward(params, X0, bf)
     n = X0.shape[0]
     z = Zs[4]
     zl = z[:, 0]
@@ -112,7 +119,7 @@ def loss_and_grad(params, X0, y, d, w_dir, bf=True):
     dZ[:, 1:4] = 2 * w_dir * y[:, None] * diff / n
     grads = []
     for l in range(4, -1, -1):
-        dW = r(dZ).T @ Xs[l]
+        dW = r(dZ).T @ r(As[l])
         db = dZ.sum(axis=0)
         grads.append((l, dW, db))
         if l > 0:

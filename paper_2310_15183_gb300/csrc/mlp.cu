@@ -11,12 +11,14 @@
 //   Split-K over gridDim.z accumulates into C with atomics.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 #include <stdint.h>
 
 #include <mutex>
 #include <stdlib.h>
+#include <string.h>
 
 #include "../../include/geotrace.h"
 #include "mlp.cuh"
@@ -81,7 +83,26 @@ __device__ __forceinline__ void stage_tile(uint8_t *sm, const __nv_bfloat16 *__r
     }
 }
 
-__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
+__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
+
+// 16-bit output element (bf16, or fp16 bits stored in the same slot) and a packed pair
+__device__ __forceinline__ __nv_bfloat16 to_c16(float y, int f16)
+{
+    if (f16) {
+        const __half h = __float2half_rn(y);
+        return __ushort_as_bfloat16(__half_as_ushort(h));
+    }
+    return __float2bfloat16(y);
+}
+__device__ __forceinline__ uint32_t pack_c16(float lo, float hi, int f16)
+{
+    if (f16) {
+        const __half2 h = __floats2half2_rn(lo, hi);
+        return *reinterpret_cast<const uint32_t *>(&h);
+    }
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
 
 
 // Epilogue shared by both kernels: TMEM -> registers (thread = row) -> bias -> shared
@@ -128,7 +149,7 @@ __device__ __forceinline__ void gemm_epilogue(const GemmArgs &g, uint32_t tmem, 
                     else
                         *p = y;
                 }
-                if (g.C16) g.C16[(int64_t)row * g.ldc16 + col] = __float2bfloat16(y);
+                if (g.C16) g.C16[(int64_t)row * g.ldc16 + col] = to_c16(y, g.c16_f16);
             }
         }
         __syncthreads();
@@ -166,7 +187,7 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(GemmArgs g)
     bool ok = true;
     const bool a_vec = (g.a_sk == 1) && (g.a_sm % 8 == 0) && ((uintptr_t)g.A % 16 == 0);
     const bool b_vec = (g.b_sk == 1) && (g.b_sn % 8 == 0) && ((uintptr_t)g.B % 16 == 0);
-    constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+    const uint32_t idesc = tc::idesc_f16_f32(BM, BN, g.f16_in == 0);
 
     for (int c = 0; c < nk; ++c) {
         const int s = c & 1;
@@ -191,7 +212,7 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(GemmArgs g)
             for (int kk = 0; kk < BK / 16; ++kk) {
                 const uint64_t ad = tc::smem_desc(a_base + kk * 2 * L::A_LBO, L::A_LBO, 128);
                 const uint64_t bd = tc::smem_desc(b_base + kk * 2 * L::B_LBO, L::B_LBO, 128);
-                tc::mma_bf16(tmem, ad, bd, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+                tc::mma_f16(tmem, ad, bd, idesc, (c > 0 || kk > 0) ? 1u : 0u);
             }
             tc::mma_commit(tc::smem_u32(&mbar[s]));
         }
@@ -273,7 +294,7 @@ __global__ void __launch_bounds__(128) tc_gemm_pipe_kernel(GemmArgs g)
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_slot;
     const uint32_t sbase = tc::smem_u32(smem);
-    constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+    const uint32_t idesc = tc::idesc_f16_f32(BM, BN, g.f16_in == 0);
 
     auto issue = [&](int c) {
         const uint32_t a_s = sbase + (c % STAGES) * L::STAGE;
@@ -299,7 +320,7 @@ __global__ void __launch_bounds__(128) tc_gemm_pipe_kernel(GemmArgs g)
             for (int kk = 0; kk < BK / 16; ++kk) {
                 const uint64_t ad = tc::smem_desc(a_base + kk * 2 * L::A_LBO, L::A_LBO, 128);
                 const uint64_t bd = tc::smem_desc(b_base + kk * 2 * L::B_LBO, L::B_LBO, 128);
-                tc::mma_bf16(tmem, ad, bd, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+                tc::mma_f16(tmem, ad, bd, idesc, (c > 0 || kk > 0) ? 1u : 0u);
             }
             tc::mma_commit(tc::smem_u32(&mbar[c % STAGES]));
         }
@@ -356,27 +377,40 @@ cudaError_t launch_pipe(const GemmArgs &g, int splits, cudaStream_t s)
 constexpr int EPI_WARPS = 8;
 constexpr int WS_THREADS = 64 + 32 * EPI_WARPS;
 
-template <int BN, int S>
+// Per-epilogue-warp staging of the TMA-store epilogue: a 32 x 32 FP32 box (128-byte
+// swizzle), a 32 x 32 bf16 box (64-byte swizzle), a 32 x 32 transposed bf16 box (no
+// swizzle) and 32 bias values.
+constexpr uint32_t STG_F32 = 0, STG_B16 = 4096, STG_B16T = 6144, STG_BIAS = 8192, STG_WARP = 9216;
+
+template <int BN, int S, bool TMA_OUT>
 struct WsSmem {
     static constexpr uint32_t A_BYTES = BM * BK * 2;
     static constexpr uint32_t B_BYTES = BN * BK * 2;
     static constexpr uint32_t STAGE = A_BYTES + B_BYTES;
-    static constexpr uint32_t EPI = EPI_WARPS * 32 * 33 * 4; // per-warp 32 x 33 float staging
+    static constexpr uint32_t EPI = TMA_OUT ? EPI_WARPS * STG_WARP : EPI_WARPS * 32 * 33 * 4;
     static constexpr uint32_t BAR = S * STAGE + EPI;
     static constexpr uint32_t NBAR = 2 * S + 5; // full[S], empty[S], acc_full[2], acc_empty[2], done
-    static constexpr uint32_t TOTAL = BAR + 8 * NBAR + 16;
+    // + 1 KB so that the base can be rounded up to the 1024-byte swizzle period
+    static constexpr uint32_t TOTAL = BAR + 8 * NBAR + 16 + 1024;
     static constexpr uint32_t A_LBO = (BM / 8) * 128;
     static constexpr uint32_t B_LBO = (BN / 8) * 128;
-    static constexpr uint32_t NCOLS = 2 * BN < 32 ? 32 : 2 * BN; // two accumulators    static_assert(TOTAL <= 227 * 1024, "shared memory per CTA");
+    static constexpr uint32_t NCOLS = 2 * BN < 32 ? 32 : 2 * BN; // two accumulators
+    static_assert(TOTAL <= 227 * 1024, "shared memory per CTA");
+    static_assert(STAGE % 1024 == 0, "stage size keeps the staging boxes 1024-byte aligned");
 };
 
-template <int BN, int S>
+struct OutMaps {
+    CUtensorMap c32, pre, c16, c16t;
+};
+
+template <int BN, int S, bool TMA_OUT>
 __global__ void __launch_bounds__(WS_THREADS, 1)
     tc_gemm_ws_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                      GemmArgs g, int splits)
+                      const __grid_constant__ OutMaps om, GemmArgs g, int splits)
 {
-    using L = WsSmem<BN, S>;
-    extern __shared__ __align__(1024) uint8_t smem[];
+    using L = WsSmem<BN, S, TMA_OUT>;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
     const uint32_t sbase = tc::smem_u32(smem);
     const uint32_t bar = sbase + L::BAR;
     auto FULL = [&](int s) { return bar + 8u * s; };
@@ -417,7 +451,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
         if (lane == 0) { // ---- producer
             uint32_t q = 0;
             for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
-                const int mt = t % m_tiles, nt = (t / m_tiles) % n_tiles, ks = t / (m_tiles * n_tiles);
+                const int nt = t % n_tiles, mt = (t / n_tiles) % m_tiles, ks = t / (m_tiles * n_tiles);
                 const int c0 = ks * per, c1 = min(nk_total, c0 + per);
                 for (int c = c0; c < c1; ++c, ++q) {
                     const int s = q % S;
@@ -440,7 +474,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) { // ---- MMA issuer
-            constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+            const uint32_t idesc = tc::idesc_f16_f32(BM, BN, g.f16_in == 0);
             uint32_t q = 0, tl = 0;
             for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++tl) {
                 const int ks = t / (m_tiles * n_tiles);
@@ -462,7 +496,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
                     for (int kk = 0; kk < BK / 16; ++kk) {
                         const uint64_t ad = tc::smem_desc(a_base + kk * 2 * L::A_LBO, L::A_LBO, 128);
                         const uint64_t bd = tc::smem_desc(b_base + kk * 2 * L::B_LBO, L::B_LBO, 128);
-                        tc::mma_bf16(d, ad, bd, idesc, (c > c0 || kk > 0) ? 1u : 0u);
+                        tc::mma_f16(d, ad, bd, idesc, (c > c0 || kk > 0) ? 1u : 0u);
                     }
                     tc::mma_commit(EMPTY(s));
                 }
@@ -473,12 +507,125 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
             tc::mma_commit(DONE);
             if (!tc::mbar_wait(DONE, 0, WAIT_LIMIT)) ok = false;
         }
+    } else if (TMA_OUT) { // ---- epilogue warps 2..9 storing through TMA
+        const int quarter = warp & 3, half = (warp - 2) >> 2;
+        uint8_t *stg = smem + S * L::STAGE + (warp - 2) * STG_WARP;
+        const uint32_t s_f32 = tc::smem_u32(stg + STG_F32), s_b16 = tc::smem_u32(stg + STG_B16),
+                       s_b16t = tc::smem_u32(stg + STG_B16T);
+        float *sbias = reinterpret_cast<float *>(stg + STG_BIAS);
+        uint32_t tl = 0;
+        for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++tl) {
+            const int nt = t % n_tiles, mt = (t / n_tiles) % m_tiles, ks = t / (m_tiles * n_tiles);
+            const int b = tl & 1;
+            const int m0 = mt * BM + quarter * 32, n0 = nt * BN;
+            // bias of this lane's column in each of the warp's chunks, fetched before the wait
+            const bool has_bias = g.bias && ks == 0;
+            constexpr int NCH = BN / 64 > 0 ? BN / 64 : 1;
+            float bl[NCH];
+#pragma unroll
+            for (int j = 0; j < NCH; j++) {
+                const int col = n0 + 32 * half + 64 * j + lane;
+                bl[j] = (has_bias && 32 * half + 64 * j < BN && col < g.N) ? __ldg(g.bias + col) : 0.f;
+            }
+            ok = tc::mbar_wait(ACCF(b), (tl >> 1) & 1, WAIT_LIMIT);
+            if (!ok) break;
+            tc::fence_after_sync();
+#pragma unroll
+            for (int j = 0; j < NCH; j++) {
+                const int cc = 32 * half + 64 * j;
+                if (cc >= BN || m0 >= g.M || n0 + cc >= g.N) break;
+                float v[32];
+                tc::tmem_ld32(tmem + (uint32_t)(b * BN + cc) + ((uint32_t)(quarter * 32) << 16), v);
+                // this warp's previous boxes have left shared memory before it is rewritten
+                if (lane == 0) tc::bulk_wait_read();
+                if (has_bias) sbias[lane] = bl[j];
+                __syncwarp();
+                if (has_bias) {
+#pragma unroll
+                    for (int i = 0; i < 32; i += 4) {
+                        const float4 bb = *reinterpret_cast<const float4 *>(sbias + i);
+                        v[i] += bb.x;
+                        v[i + 1] += bb.y;
+                        v[i + 2] += bb.z;
+                        v[i + 3] += bb.w;
+                    }
+                }
+                // FP32 box, row = lane, 16-byte chunk c at c ^ (row % 8)
+                auto put_f32 = [&]() {
+#pragma unroll
+                    for (int c = 0; c < 8; c++)
+                        *reinterpret_cast<float4 *>(stg + STG_F32 + lane * 128 + ((c ^ (lane & 7)) << 4)) =
+                            make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+                    tc::fence_proxy_async();
+                    __syncwarp();
+                };
+                if (g.pre) {
+                    put_f32();
+                    if (lane == 0) {
+                        tc::tma_store_2d(&om.pre, n0 + cc, m0, s_f32);
+                        tc::bulk_commit();
+                    }
+                }
+                if (g.act == 1) {
+#pragma unroll
+                    for (int i = 0; i < 32; i++) v[i] = silu(v[i]);
+                }
+                if (g.C32) {
+                    if (g.pre) {
+                        if (lane == 0) tc::bulk_wait_read();
+                        __syncwarp();
+                    }
+                    put_f32();
+                    if (lane == 0) {
+                        if (g.atomic)
+                            tc::tma_reduce_add_2d(&om.c32, n0 + cc, m0, s_f32);
+                        else
+                            tc::tma_store_2d(&om.c32, n0 + cc, m0, s_f32);
+                        tc::bulk_commit();
+                    }
+                }
+                if (g.C16) { // 16-bit box, row = lane (64 bytes), chunk c at c ^ ((row / 2) % 4)
+#pragma unroll
+                    for (int c = 0; c < 4; c++) {
+                        uint4 w;
+                        uint32_t *wp = &w.x;
+#pragma unroll
+                        for (int j = 0; j < 4; j++) {
+                            wp[j] = pack_c16(v[8 * c + 2 * j], v[8 * c + 2 * j + 1], g.c16_f16);
+                        }
+                        *reinterpret_cast<uint4 *>(stg + STG_B16 + lane * 64 +
+                                                   ((c ^ ((lane >> 1) & 3)) << 4)) = w;
+                    }
+                }
+                if (g.C16T) { // transposed bf16 box: row = column i, element = lane
+#pragma unroll
+                    for (int i = 0; i < 32; i++)
+                        reinterpret_cast<__nv_bfloat16 *>(stg + STG_B16T)[i * 32 + lane] =
+                            __float2bfloat16(v[i]);
+                }
+                if (g.C16 || g.C16T) {
+                    tc::fence_proxy_async();
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (g.C16) tc::tma_store_2d(&om.c16, n0 + cc, m0, s_b16);
+                        if (g.C16T) tc::tma_store_2d(&om.c16t, m0, n0 + cc, s_b16t);
+                        tc::bulk_commit();
+                    }
+                }
+                __syncwarp();
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(ACCE(b));
+        }
+        if (lane == 0) tc::bulk_wait_all();
+        __syncwarp();
     } else { // ---- epilogue warps 2..9: TMEM lanes 32 * (warp % 4), column chunks by half
         const int quarter = warp & 3, half = (warp - 2) >> 2;
         float *stg = reinterpret_cast<float *>(smem + S * L::STAGE) + (warp - 2) * 32 * 33;
         uint32_t tl = 0;
         for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++tl) {
-            const int mt = t % m_tiles, nt = (t / m_tiles) % n_tiles, ks = t / (m_tiles * n_tiles);
+            const int nt = t % n_tiles, mt = (t / n_tiles) % m_tiles, ks = t / (m_tiles * n_tiles);
             const int b = tl & 1;
             ok = tc::mbar_wait(ACCF(b), (tl >> 1) & 1, WAIT_LIMIT);
             if (!ok) break;
@@ -521,7 +668,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
                                 else
                                     *p = y;
                             }
-                            if (g.C16) g.C16[row * g.ldc16 + col] = __float2bfloat16(y);
+                            if (g.C16) g.C16[row * g.ldc16 + col] = to_c16(y, g.c16_f16);
                         }
                     }
                 }
@@ -572,19 +719,58 @@ bool make_map(CUtensorMap *m, const void *base, uint64_t rows, uint64_t cols, ui
 
 int g_sm_count = 0;
 
+// Output tensor map (2-D, row stride `ld` elements) with 32 x 32 boxes.
+bool make_out_map(CUtensorMap *m, void *base, CUtensorMapDataType dt, int esize, uint64_t rows,
+                  uint64_t cols, uint64_t ld, CUtensorMapSwizzle sw)
+{
+    auto enc = tensor_map_encoder();
+    if (!enc || rows == 0 || cols == 0 || ((uintptr_t)base & 15) || (ld * esize) % 16) return false;
+    cuuint64_t dims[2] = {cols, rows};
+    cuuint64_t strides[1] = {ld * esize};
+    cuuint32_t box[2] = {32, 32};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(m, dt, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+               CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN, int S, bool TMA_OUT>
+cudaError_t launch_ws_kernel(const CUtensorMap &ta, const CUtensorMap &tb, const OutMaps &om,
+                             const GemmArgs &g, int splits, int grid, cudaStream_t s)
+{
+    using L = WsSmem<BN, S, TMA_OUT>;
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_ws_kernel<BN, S, TMA_OUT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, L::TOTAL);
+    if (e != cudaSuccess) return e;
+    tc_gemm_ws_kernel<BN, S, TMA_OUT><<<grid, WS_THREADS, L::TOTAL, s>>>(ta, tb, om, g, splits);
+    return cudaGetLastError();
+}
+
 template <int BN>
 cudaError_t launch_ws(const GemmArgs &g, int splits, cudaStream_t s, bool *used)
 {
-    constexpr int S = 4;
-    using L = WsSmem<BN, S>;
     *used = false;
     CUtensorMap ta, tb;
     if (!make_map(&ta, g.A, (uint64_t)g.M, (uint64_t)g.K, (uint64_t)g.a_sm, BM) ||
         !make_map(&tb, g.B, (uint64_t)g.N, (uint64_t)g.K, (uint64_t)g.b_sn, BN))
         return cudaSuccess; // caller falls back
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_ws_kernel<BN, S>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, L::TOTAL);
-    if (e != cudaSuccess) return e;
+    // TMA-store epilogue when every requested output has an encodable map
+    OutMaps om;
+    memset(&om, 0, sizeof(om));
+    bool tma_out = BN >= 32;
+    if (tma_out && g.C32)
+        tma_out = make_out_map(&om.c32, g.C32, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g.M, g.N, g.ldc,
+                               CU_TENSOR_MAP_SWIZZLE_128B);
+    if (tma_out && g.pre)
+        tma_out = make_out_map(&om.pre, g.pre, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g.M, g.N,
+                               g.ld_pre, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (tma_out && g.C16)
+        tma_out = make_out_map(&om.c16, g.C16,
+                               g.c16_f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                               2, g.M, g.N,
+                               g.ldc16, CU_TENSOR_MAP_SWIZZLE_64B);
+    if (tma_out && g.C16T)
+        tma_out = make_out_map(&om.c16t, g.C16T, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, g.N, g.M, g.ldt,
+                               CU_TENSOR_MAP_SWIZZLE_NONE);
     if (g_sm_count == 0) {
         int dev = 0;
         cudaGetDevice(&dev);
@@ -595,9 +781,10 @@ cudaError_t launch_ws(const GemmArgs &g, int splits, cudaStream_t s, bool *used)
     splits = (nk_total + ((nk_total + splits - 1) / splits) - 1) / ((nk_total + splits - 1) / splits);
     const int64_t total = (int64_t)((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN) * splits;
     const int grid = (int)(total < g_sm_count ? total : g_sm_count);
-    tc_gemm_ws_kernel<BN, S><<<grid, WS_THREADS, L::TOTAL, s>>>(ta, tb, g, splits);
+    constexpr int S = BN >= 256 ? 3 : 4;
     *used = true;
-    return cudaGetLastError();
+    return tma_out ? launch_ws_kernel<BN, S, true>(ta, tb, om, g, splits, grid, s)
+                   : launch_ws_kernel<BN, S, false>(ta, tb, om, g, splits, grid, s);
 }
 
 template <int BN>

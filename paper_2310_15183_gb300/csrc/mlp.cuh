@@ -25,6 +25,8 @@ struct GemmArgs {
     __nv_bfloat16 *C16T; // optional transposed bf16 output: C16T[n * ldt + m]
     int64_t ldt;
     int *err;          // set to 1 when an mbarrier wait ran out
+    int f16_in;        // A and B hold IEEE fp16 bit patterns instead of bf16 (both, never mixed)
+    int c16_f16;       // C16 receives fp16 instead of bf16 (C16T stays bf16)
 };
 
 // bn in {16, 32, 64, 128, 256}; splits = K splits (gridDim.z).

@@ -1,14 +1,18 @@
 // surrogate.cu -- the MLP surrogate of the ray tracer: per-pixel (alpha, beta, spin,
 // q, theta0) -> (escape logit, end direction), trained on rays the integrator itself
-// produces, evaluated with the tcgen05 BF16 GEMM, and backed by the integrator for
+// produces, evaluated with the tcgen05 GEMM, and backed by the integrator for
 // low-confidence and photon-ring pixels.
 //
 // Network: 16 (5 inputs and 5 columns derived from them, zero padded) -> 256 -> 256 ->
 // 256 -> 256 -> 16 (4 used:
 // logit and the unit vector of the end direction, which unlike (theta, phi) has no
-// jump at phi = +-pi), SiLU between layers.  FP32 master weights and AdamW state;
-// BF16 weights and activations feed the tensor cores; accumulation is FP32.
+// jump at phi = +-pi), SiLU between layers.  FP32 master weights and AdamW state.
+// The forward products take FP16 weights and activations (10-bit mantissa: the end
+// direction is read from the last layer, and BF16's 7 bits put a rounding floor of about
+// 2e-3 rad under it); the backward products take BF16, whose range holds gradients
+// scaled by 1/batch.  Accumulation is FP32 throughout.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -81,10 +85,11 @@ __device__ __forceinline__ void make_features(double al, double bt, double spin,
     for (int j = 10; j < 16; j++) f[j] = 0.0f;
 }
 
-// features of samples [row0, row0 + n): X0[r, 0..15] (bf16)
+// features of samples [row0, row0 + n): X0[r, 0..15] (fp16, input of the forward
+// product) and optionally X0T (bf16, transposed, input of the weight-gradient product)
 __global__ void features_kernel(int64_t n, int64_t row0, const double *alpha, const double *beta,
                                 const double *spin, const double *q, const double *theta0,
-                                Norm nm, __nv_bfloat16 *X0, __nv_bfloat16 *X0T = nullptr)
+                                Norm nm, __half *X0, __nv_bfloat16 *X0T = nullptr)
 {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
@@ -92,7 +97,7 @@ __global__ void features_kernel(int64_t n, int64_t row0, const double *alpha, co
     float f[16];
     make_features(alpha[k], beta[k], spin[k], q[k], theta0[k], nm, f);
 #pragma unroll
-    for (int j = 0; j < 16; j++) X0[r * 16 + j] = __float2bfloat16(f[j]);
+    for (int j = 0; j < 16; j++) X0[r * 16 + j] = __float2half_rn(f[j]);
     if (X0T)
 #pragma unroll
         for (int j = 0; j < 16; j++) X0T[j * n + r] = __float2bfloat16(f[j]);
@@ -100,7 +105,7 @@ __global__ void features_kernel(int64_t n, int64_t row0, const double *alpha, co
 
 // features of camera pixels [pix0, pix0 + n) (flat j*res_x + i)
 __global__ void camera_features_kernel(int64_t n, int64_t pix0, const CamDesc *cam, Norm nm,
-                                       __nv_bfloat16 *X0)
+                                       __half *X0)
 {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
@@ -112,7 +117,7 @@ __global__ void camera_features_kernel(int64_t n, int64_t pix0, const CamDesc *c
     float f[16];
     make_features(al, bt, (c.S / c.M) / c.M, c.Q, c.th0, nm, f);
 #pragma unroll
-    for (int jj = 0; jj < 16; jj++) X0[r * 16 + jj] = __float2bfloat16(f[jj]);
+    for (int jj = 0; jj < 16; jj++) X0[r * 16 + jj] = __float2half_rn(f[jj]);
 }
 
 // Loss of rows [0, B): BCE(logit, y) + w_dir * y * |d_pred - d|^2, averaged over B.
@@ -206,10 +211,10 @@ __global__ void adamw_kernel(int64_t n, float *p, const float *g, float *m, floa
     p[i] = pi;
 }
 
-__global__ void to_bf16_kernel(int64_t n, const float *src, __nv_bfloat16 *dst)
+__global__ void to_f16_kernel(int64_t n, const float *src, __half *dst)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = __float2bfloat16(src[i]);
+    if (i < n) dst[i] = __float2half_rn(src[i]);
 }
 
 // Photon-ring test for a Kerr pixel: with E = -p_t, L = p_phi and the Carter constant
@@ -325,12 +330,12 @@ struct gt_surrogate {
     int64_t n_params = 0;
     float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr; // fp32 params, grads, Adam
     uint8_t *decay = nullptr;
-    __nv_bfloat16 *wb = nullptr; // bf16 copy of all params (only weights used)
+    __half *wh = nullptr; // fp16 copy of all params for the forward products (weights only)
     int64_t step = 0;
     // workspace for `rows` rows
     int64_t rows = 0;
-    __nv_bfloat16 *X[N_LAYERS] = {}; // inputs of each layer (bf16)
-    __nv_bfloat16 *XT[N_LAYERS] = {}; // the same, transposed (in_dim x rows)
+    __half *X[N_LAYERS] = {};         // inputs of each layer (fp16, forward products)
+    __nv_bfloat16 *XT[N_LAYERS] = {}; // the same in bf16, transposed (in_dim x rows)
     __nv_bfloat16 *WT = nullptr;      // transposed bf16 weights ([in][out] per layer)
     __nv_bfloat16 *dZT = nullptr;     // transposed bf16 gradient (cols x rows)
     float *Z[N_LAYERS] = {};         // pre-activations (fp32)
@@ -368,7 +373,7 @@ int ensure_ws(gt_surrogate *s, int64_t rows)
     free_ws(s);
     cudaError_t e = cudaSuccess;
     for (int l = 0; l < N_LAYERS && e == cudaSuccess; l++) {
-        e = cudaMalloc(&s->X[l], rows * IN_DIM[l] * sizeof(__nv_bfloat16));
+        e = cudaMalloc(&s->X[l], rows * IN_DIM[l] * sizeof(__half));
         if (e == cudaSuccess) e = cudaMalloc(&s->XT[l], rows * IN_DIM[l] * sizeof(__nv_bfloat16));
         if (e == cudaSuccess) e = cudaMalloc(&s->Z[l], rows * OUT_DIM[l] * sizeof(float));
     }
@@ -399,19 +404,22 @@ struct Dev {
     }
 };
 
-cudaError_t gemm(const __nv_bfloat16 *A, int64_t a_sm, int64_t a_sk, const __nv_bfloat16 *B,
-                 int64_t b_sn, int64_t b_sk, int M, int N, int K, const float *bias, int act,
-                 float *pre, float *C32, int64_t ldc, bool atomic, __nv_bfloat16 *C16, int splits,
-                 int *err, cudaStream_t st, __nv_bfloat16 *C16T = nullptr)
+// f16: A, B and C16 are fp16 (the forward products); otherwise bf16.  C16T is bf16.
+cudaError_t gemm(const void *A, int64_t a_sm, int64_t a_sk, const void *B, int64_t b_sn,
+                 int64_t b_sk, int M, int N, int K, const float *bias, int act, float *pre,
+                 float *C32, int64_t ldc, bool atomic, void *C16, int splits, int *err,
+                 cudaStream_t st, __nv_bfloat16 *C16T = nullptr, bool f16 = false)
 {
     GemmArgs g = {};
+    g.f16_in = f16 ? 1 : 0;
+    g.c16_f16 = f16 ? 1 : 0;
     g.M = M;
     g.N = N;
     g.K = K;
-    g.A = A;
+    g.A = static_cast<const __nv_bfloat16 *>(A);
     g.a_sm = a_sm;
     g.a_sk = a_sk;
-    g.B = B;
+    g.B = static_cast<const __nv_bfloat16 *>(B);
     g.b_sn = b_sn;
     g.b_sk = b_sk;
     g.bias = bias;
@@ -421,7 +429,7 @@ cudaError_t gemm(const __nv_bfloat16 *A, int64_t a_sm, int64_t a_sk, const __nv_
     g.C32 = C32;
     g.ldc = ldc;
     g.atomic = atomic ? 1 : 0;
-    g.C16 = C16;
+    g.C16 = static_cast<__nv_bfloat16 *>(C16);
     g.ldc16 = N;
     g.C16T = C16T;
     g.ldt = M;
@@ -438,10 +446,10 @@ cudaError_t forward(gt_surrogate *s, int B, cudaStream_t st, bool keep_pre = tru
     cudaError_t e = cudaSuccess;
     for (int l = 0; l < N_LAYERS && e == cudaSuccess; l++) {
         const bool last = (l == N_LAYERS - 1);
-        e = gemm(s->X[l], IN_DIM[l], 1, s->wb + s->w_off[l], IN_DIM[l], 1, B, OUT_DIM[l], IN_DIM[l],
+        e = gemm(s->X[l], IN_DIM[l], 1, s->wh + s->w_off[l], IN_DIM[l], 1, B, OUT_DIM[l], IN_DIM[l],
                  s->p + s->b_off[l], last ? 0 : 1, (last || !keep_pre) ? nullptr : s->Z[l],
                  last ? s->Z[l] : nullptr, OUT_DIM[l], false, last ? nullptr : s->X[l + 1], 1,
-                 s->err, st, (last || !keep_pre) ? nullptr : s->XT[l + 1]);
+                 s->err, st, (last || !keep_pre) ? nullptr : s->XT[l + 1], true);
     }
     return e;
 }
@@ -484,10 +492,11 @@ int check_err(gt_surrogate *s, cudaStream_t st)
     return h ? GT_ERR_TIMEOUT : GT_OK;
 }
 
-// bf16 copies of the parameters and transposed bf16 weights after an update
-cudaError_t refresh_bf16(gt_surrogate *s, cudaStream_t st)
+// fp16 copy of the parameters (forward products) and transposed bf16 weights (backward
+// products) after an update
+cudaError_t refresh_copies(gt_surrogate *s, cudaStream_t st)
 {
-    to_bf16_kernel<<<blocks_for(s->n_params), 256, 0, st>>>(s->n_params, s->p, s->wb);
+    to_f16_kernel<<<blocks_for(s->n_params), 256, 0, st>>>(s->n_params, s->p, s->wh);
     for (int l = 0; l < N_LAYERS; l++)
         weights_t_kernel<<<blocks_for((int64_t)OUT_DIM[l] * IN_DIM[l]), 256, 0, st>>>(
             s->p + s->w_off[l], OUT_DIM[l], IN_DIM[l], s->WT + s->w_off[l]);
@@ -554,7 +563,7 @@ int gt_surrogate_create(int device, const gt_surrogate_norm *nrm, uint64_t seed,
     if (e == cudaSuccess) e = cudaMalloc(&s->g, off * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&s->m, off * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&s->v, off * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&s->wb, off * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMalloc(&s->wh, off * sizeof(__half));
     if (e == cudaSuccess) e = cudaMalloc(&s->WT, off * sizeof(__nv_bfloat16));
     if (e == cudaSuccess) e = cudaMalloc(&s->decay, off);
     if (e == cudaSuccess) e = cudaMalloc(&s->loss, sizeof(float));
@@ -571,7 +580,7 @@ int gt_surrogate_create(int device, const gt_surrogate_norm *nrm, uint64_t seed,
     if (e == cudaSuccess) e = cudaMemset(s->err, 0, sizeof(int));
     if (e == cudaSuccess) {
         init_params_kernel<<<blocks_for(off), 256>>>(s->p, off, d_offs, d_scales, (int)offs.size(), seed);
-        e = refresh_bf16(s, 0);
+        e = refresh_copies(s, 0);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
     }
     cudaFree(d_offs);
@@ -594,7 +603,7 @@ int gt_surrogate_destroy(gt_surrogate *s)
     cudaFree(s->g);
     cudaFree(s->m);
     cudaFree(s->v);
-    cudaFree(s->wb);
+    cudaFree(s->wh);
     cudaFree(s->WT);
     cudaFree(s->decay);
     cudaFree(s->loss);
@@ -616,7 +625,7 @@ int gt_surrogate_set_params(gt_surrogate *s, const float *host, int64_t n)
     if (!s || !host || n != s->n_params) return GT_ERR_INVALID_ARG;
     Dev d(s->device);
     cudaError_t e = cudaMemcpy(s->p, host, n * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = refresh_bf16(s, 0);
+    if (e == cudaSuccess) e = refresh_copies(s, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     return e == cudaSuccess ? GT_OK : GT_ERR_CUDA;
 }
@@ -704,7 +713,7 @@ int gt_surrogate_train(gt_ctx *ctx, gt_surrogate *s, const gt_train_cfg *cfg, in
                                                                   lr, b1, b2, eps,
                                                                   (float)cfg->weight_decay, bc1, bc2,
                                                                   s->decay);
-            e = refresh_bf16(s, st);
+            e = refresh_copies(s, st);
         }
         if (e != cudaSuccess) return GT_ERR_CUDA;
         if (loss_per_epoch) {

@@ -28,13 +28,15 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-// 32-bit instruction descriptor of kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
-// (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at 17, M >> 4 at 24.
-__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
+// 32-bit instruction descriptor of kind::f16: D = F32 (bits 4-5 = 1), A and B both BF16
+// (bits 7-9 = 1, 10-12 = 1) or both FP16 (0), both K-major (bits 15, 16 = 0), N >> 3 at
+// 17, M >> 4 at 24.
+__host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N, bool bf16)
 {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-           ((uint32_t)(M >> 4) << 24);
+    return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) { return idesc_f16_f32(M, N, true); }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols)
 {
@@ -48,7 +50,7 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
                                          uint32_t idesc, uint32_t accumulate)
 {
     asm volatile(
@@ -144,6 +146,37 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void *tmap, int 
         "l"(tmap), "r"(x), "r"(y), "r"(mbar)
         : "memory");
 }
+
+} // namespace tc
+} // namespace gt
+
+namespace gt {
+namespace tc {
+
+// ---------------------------------------------------------------- TMA stores
+// 2-D tiled store (or FP32 add-reduction) of a shared-memory box to global memory; rows
+// and columns outside the tensor are clipped.  Issued by one thread after the box's
+// writers fenced their shared-memory stores to the async proxy.
+__device__ __forceinline__ void tma_store_2d(const void *tmap, int x, int y, uint32_t src)
+{
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     tmap),
+                 "r"(x), "r"(y), "r"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_reduce_add_2d(const void *tmap, int x, int y, uint32_t src)
+{
+    asm volatile(
+        "cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+            tmap),
+        "r"(x), "r"(y), "r"(src)
+        : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the shared-memory sources of all committed bulk stores have been read
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// all committed bulk stores have completed
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 } // namespace tc
 } // namespace gt

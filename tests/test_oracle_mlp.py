@@ -52,3 +52,25 @@ def test_features_cover_unit_range():
     assert np.allclose(X[:, 5], np.hypot(X[:, 0], X[:, 1]))
     assert np.allclose(X[:, 6] ** 2 + X[:, 7] ** 2, 1.0)
     assert np.allclose(X[:, 8] ** 2 + X[:, 9] ** 2, 1.0) and np.all(X[:, 10:] == 0)
+
+
+def test_f16_rounding_is_round_to_nearest_even():
+    x = np.array([1.0, 1.0 + 2 ** -11, 1.0 + 3 * 2 ** -11, 1.0 + 2 ** -10, -2.5, 65504.0])
+    r = mlp.f16(x)
+    assert r[0] == 1.0 and r[1] == 1.0 and r[2] == 1.0 + 2 ** -9
+    assert r[3] == 1.0 + 2 ** -10 and r[4] == -2.5 and r[5] == 65504.0
+
+
+def test_rounded_network_stays_close_to_exact():
+    """The 16-bit rounding points perturb the loss and gradient only slightly (a
+    transposed or misplaced rounding would not)."""
+    p = mlp.init_params(4)
+    rng = np.random.Generator(np.random.PCG64(8))
+    X0 = mlp.features(rng.uniform(-0.04, 0.04, 64), rng.uniform(-0.04, 0.04, 64),
+                      rng.uniform(0, 0.99, 64), np.zeros(64), rng.uniform(0.1, 1.5, 64))
+    y = (rng.uniform(size=64) < 0.5).astype(float)
+    d = np.stack([np.ones(64), np.zeros(64), np.zeros(64)], 1) * y[:, None]
+    l0, g0, _ = mlp.loss_and_grad(p, X0, y, d, 10.0, bf=False)
+    l1, g1, _ = mlp.loss_and_grad(p, X0, y, d, 10.0, bf=True)
+    assert abs(l1 - l0) < 1e-2 * abs(l0)
+    assert np.linalg.norm(g1 - g0) < 2e-2 * np.linalg.norm(g0)

@@ -15,8 +15,10 @@
 //     2H = -p_t^2/f + F (p_phi + w p_t)^2 + G (Delta p_r^2 + p_theta^2),
 //     F = f/(Delta sin^2),  G = g^{theta theta} = (1-alpha^2)^2/k^2 exp(2psi - 2gamma'')/B,
 //   (gamma'' = gamma' without its logarithm, which cancels against e^{2gamma}'s
-//   (x^2-1) factor), and the r and theta derivatives come from forward-mode dual
-//   numbers (value, d/dr, d/dtheta) carried through every operation.
+//   (x^2-1) factor); the kernels take its r and theta derivatives by a reverse
+//   (adjoint) sweep over the same expressions (mn_rates), and a forward-mode form with
+//   dual numbers (value, d/dr, d/dtheta) is kept as the reference it is checked
+//   against (mn_rates_fwd).
 //
 // Both are written once over a scalar type T so the FP32-mixed path can reuse them.
 #pragma once
@@ -300,9 +302,218 @@ GT_HD void mn_potentials(const SpacetimeT<T> &c, T r, T th, MNPot<N> &P)
     P.Delta = x2m1 * T(c.k2);
 }
 
+// Rates of Manko-Novikov by reverse-mode differentiation: one forward sweep of values
+// through the same expressions as mn_potentials, then one backward sweep of adjoints
+// (xb = d(2H)/dx for each intermediate x) from 2H down to r and theta.  Exact to
+// rounding like the dual-number form below (mn_rates_fwd), with less than half its
+// arithmetic: a product costs one multiply forward and two fused multiply-adds backward
+// instead of five operations for a value and two derivatives.
 template <class T>
 GT_HD void mn_rates(const SpacetimeT<T> &c, T r, T th, T pr, T pth, T pt, T pph,
-                                         Rates<T> &o)
+                    Rates<T> &o)
+{
+    // ---- forward sweep (values)
+    T s, cs;
+    sincos_t(th, &s, &cs);
+    const T ik = T(c.ik), tb = T(c.two_beta), al = T(c.alpha);
+    const T x = (r - T(c.M)) * ik;
+    const T xm1 = (r - T(c.r_plus)) * ik; // x - 1 without cancellation
+    const T y = cs, s2 = s * s;
+    const T xp1 = x + T(1);
+    const T x2m1 = xm1 * xp1;
+    const T R2 = fma_t(y, y, x2m1);
+    const T iR = rsqrt_t(R2);
+    const T xy = x * y;
+    const T u = xy * iR;
+    const T u2 = u * u;
+    const T P2 = fma_t(T(1.5), u2, T(-0.5));
+    const T q3 = fma_t(T(2.5), u2, T(-1.5));
+    const T P3 = u * q3;
+    const T iR2 = iR * iR;
+    const T iR3 = iR2 * iR;
+    const T uR2 = u * iR2;
+    const T P2R3 = P2 * iR3;
+    const T T1 = iR + uR2 + P2R3;
+    const T T2 = uR2 - iR - P2R3;
+    const T xmy = x - y, xpy = x + y;
+    const T Sa = xmy * T1;
+    const T Sb = xpy * T2;
+    const T iRP = iR + P2R3;
+    const T Sg = T(2) * (x * iRP - y * uR2);
+    const T fa = exp_t((Sa - T(1)) * (-tb)) * (-al);
+    const T fb = exp_t((Sb + T(1)) * tb) * al;
+    const T ab = fa * fb;
+    const T opab = ab + T(1);
+    const T bma = fb - fa;
+    const T A = x2m1 * (opab * opab) - s2 * (bma * bma);
+    const T yp1 = y + T(1), omy = T(1) - y;
+    const T Bq1 = fma_t(xm1, ab, xp1);
+    const T Bq2 = yp1 * fa + omy * fb;
+    const T B = Bq1 * Bq1 + Bq2 * Bq2;
+    const T fsum = fa + fb, omab = T(1) - ab;
+    const T C1 = bma - y * fsum;
+    const T C2 = fma_t(x, omab, opab);
+    const T c1 = x2m1 * opab, c2 = s2 * bma;
+    const T C = c1 * C1 + c2 * C2;
+    const T psi2 = tb * P2R3;
+    const T D = P3 * P3 - P2 * P2;
+    const T t3 = T(c.three_beta2) * (iR3 * iR3);
+    const T g2 = fma_t(t3, D, (Sg - T(2)) * tb);
+    const T e2psi = exp_t(psi2);
+    const T ie2psi = rcp_t(e2psi);
+    const T iA = rcp_t(A);
+    const T iB = rcp_t(B);
+    const T v1 = ie2psi * B;
+    const T invf = v1 * iA;
+    const T xs = x2m1 * s2;
+    const T ixs = rcp_t(xs);
+    const T pA = A * iB;
+    const T pB = pA * ixs;
+    const T W = pB * T(c.inv_k2);
+    const T F = e2psi * W;
+    const T ieC = ie2psi * C;
+    const T om0 = ieC * iA;
+    const T om = om0 * T(c.two_k) - T(c.w_inf);
+    const T eG = exp_t(psi2 - g2);
+    const T iBc = iB * T(c.c_g);
+    const T G = eG * iBc;
+    const T Delta = x2m1 * T(c.k2);
+    const T pw = fma_t(om, pt, pph);
+    const T pr2 = pr * pr;
+    const T Q = fma_t(Delta, pr2, pth * pth);
+    const T Fpw = F * pw;
+    o.dt = fma_t(Fpw, om, -pt * invf);
+    o.dph = Fpw;
+    o.dr = G * Delta * pr;
+    o.dth = G * pth;
+
+    // ---- backward sweep: adjoints of 2H = -pt^2 invf + F pw^2 + G Q
+    const T invf_b = -pt * pt;
+    const T F_b = pw * pw;
+    const T om0_b = T(2) * Fpw * pt * T(c.two_k); // through pw = om pt + pph
+    const T G_b = Q;
+    const T Delta_b = G * pr2;
+    // G = eG iB c_g, eG = exp(psi2 - g2)
+    const T eG_b = G_b * iBc;
+    const T dG = eG_b * eG;
+    T psi2_b = dG;
+    const T g2_b = -dG;
+    T iB_b = G_b * eG * T(c.c_g);
+    // om0 = ie2psi C iA
+    T ie2psi_b = om0_b * C * iA;
+    T C_b = om0_b * ie2psi * iA;
+    T iA_b = om0_b * ieC;
+    // F = e2psi pB inv_k2, pB = A iB ixs
+    T e2psi_b = F_b * W;
+    const T pB_b = F_b * e2psi * T(c.inv_k2);
+    const T pA_b = pB_b * ixs;
+    const T ixs_b = pB_b * pA;
+    T A_b = pA_b * iB;
+    iB_b = fma_t(pA_b, A, iB_b);
+    // invf = ie2psi B iA
+    const T v1_b = invf_b * iA;
+    iA_b = fma_t(invf_b, v1, iA_b);
+    ie2psi_b = fma_t(v1_b, B, ie2psi_b);
+    T B_b = v1_b * ie2psi;
+    // reciprocals and the exponential of psi
+    const T xs_b = -ixs_b * ixs * ixs;
+    T x2m1_b = fma_t(Delta_b, T(c.k2), xs_b * s2);
+    T s2_b = xs_b * x2m1;
+    B_b = fma_t(-iB_b * iB, iB, B_b);
+    A_b = fma_t(-iA_b * iA, iA, A_b);
+    e2psi_b = fma_t(-ie2psi_b * ie2psi, ie2psi, e2psi_b);
+    psi2_b = fma_t(e2psi_b, e2psi, psi2_b);
+    // g2 = t3 D + tb (Sg - 2), t3 = 3 beta^2 iR3^2
+    const T D_b = g2_b * t3;
+    T iR3_b = g2_b * D * T(c.three_beta2) * T(2) * iR3;
+    const T Sg_b = g2_b * tb;
+    T P3_b = T(2) * P3 * D_b;
+    T P2_b = T(-2) * P2 * D_b;
+    T P2R3_b = tb * psi2_b;
+    // C = c1 C1 + c2 C2
+    const T C1_b = C_b * c1, C2_b = C_b * c2;
+    const T c1_b = C_b * C1, c2_b = C_b * C2;
+    x2m1_b = fma_t(c1_b, opab, x2m1_b);
+    T opab_b = c1_b * x2m1 + C2_b;
+    s2_b = fma_t(c2_b, bma, s2_b);
+    T bma_b = fma_t(c2_b, s2, C1_b);
+    T x_b = C2_b * omab;
+    T ab_b = -C2_b * x;
+    T y_b = -C1_b * fsum;
+    T fa_b = -C1_b * y;
+    T fb_b = fa_b;
+    // B = Bq1^2 + Bq2^2
+    const T Bq1_b = T(2) * Bq1 * B_b, Bq2_b = T(2) * Bq2 * B_b;
+    y_b = fma_t(Bq2_b, fa - fb, y_b);
+    fa_b = fma_t(Bq2_b, yp1, fa_b);
+    fb_b = fma_t(Bq2_b, omy, fb_b);
+    T xp1_b = Bq1_b;
+    T xm1_b = Bq1_b * ab;
+    ab_b = fma_t(Bq1_b, xm1, ab_b);
+    // A = x2m1 opab^2 - s2 bma^2
+    x2m1_b = fma_t(A_b, opab * opab, x2m1_b);
+    opab_b = fma_t(A_b * x2m1, T(2) * opab, opab_b);
+    s2_b = fma_t(-A_b, bma * bma, s2_b);
+    bma_b = fma_t(-A_b * s2, T(2) * bma, bma_b);
+    // bma = fb - fa, opab = ab + 1, ab = fa fb
+    fb_b = fb_b + bma_b;
+    fa_b = fa_b - bma_b;
+    ab_b = ab_b + opab_b;
+    fa_b = fma_t(ab_b, fb, fa_b);
+    fb_b = fma_t(ab_b, fa, fb_b);
+    // fa = -alpha exp(-2 beta (Sa - 1)), fb = alpha exp(2 beta (Sb + 1))
+    const T Sa_b = -fa_b * fa * tb;
+    const T Sb_b = fb_b * fb * tb;
+    // Sg = 2 (x (iR + P2R3) - y uR2)
+    const T Sg2 = T(2) * Sg_b;
+    x_b = fma_t(Sg2, iRP, x_b);
+    T iR_b = Sg2 * x;
+    P2R3_b = fma_t(Sg2, x, P2R3_b);
+    y_b = fma_t(-Sg2, uR2, y_b);
+    T uR2_b = -Sg2 * y;
+    // Sa = (x - y) T1, Sb = (x + y) T2
+    x_b = x_b + Sa_b * T1 + Sb_b * T2;
+    y_b = y_b - Sa_b * T1 + Sb_b * T2;
+    const T T1_b = Sa_b * xmy, T2_b = Sb_b * xpy;
+    iR_b = iR_b + T1_b - T2_b;
+    uR2_b = uR2_b + T1_b + T2_b;
+    P2R3_b = P2R3_b + T1_b - T2_b;
+    // P2R3 = P2 iR3, uR2 = u iR2, iR3 = iR2 iR, iR2 = iR^2
+    P2_b = fma_t(P2R3_b, iR3, P2_b);
+    iR3_b = fma_t(P2R3_b, P2, iR3_b);
+    T u_b = uR2_b * iR2;
+    T iR2_b = fma_t(uR2_b, u, iR3_b * iR);
+    iR_b = fma_t(iR3_b, iR2, iR_b);
+    iR_b = fma_t(T(2) * iR, iR2_b, iR_b);
+    // P3 = u q3, q3 = 2.5 u2 - 1.5, P2 = 1.5 u2 - 0.5, u2 = u^2
+    u_b = fma_t(P3_b, q3, u_b);
+    const T u2_b = P3_b * u * T(2.5) + T(1.5) * P2_b;
+    u_b = fma_t(T(2) * u, u2_b, u_b);
+    // u = xy iR, xy = x y
+    const T xy_b = u_b * iR;
+    iR_b = fma_t(u_b, xy, iR_b);
+    x_b = fma_t(xy_b, y, x_b);
+    y_b = fma_t(xy_b, x, y_b);
+    // iR = R2^(-1/2), R2 = x2m1 + y^2
+    const T R2_b = T(-0.5) * iR_b * iR3;
+    x2m1_b = x2m1_b + R2_b;
+    y_b = fma_t(T(2) * y, R2_b, y_b);
+    // x2m1 = xm1 xp1, xp1 = x + 1
+    xm1_b = fma_t(x2m1_b, xp1, xm1_b);
+    xp1_b = fma_t(x2m1_b, xm1, xp1_b);
+    x_b = x_b + xp1_b;
+    // x, x - 1 linear in r; y = cos theta, s2 = sin^2 theta
+    const T dHr = (x_b + xm1_b) * ik;
+    const T dHth = s * (T(2) * cs * s2_b - y_b);
+    o.dpr = T(-0.5) * dHr;
+    o.dpth = T(-0.5) * dHth;
+}
+
+// The same rates by forward-mode dual numbers (value, d/dr, d/dtheta) through
+// mn_potentials: the reference form the reverse sweep above is checked against.
+template <class T>
+GT_HD void mn_rates_fwd(const SpacetimeT<T> &c, T r, T th, T pr, T pth, T pt, T pph,
+                        Rates<T> &o)
 {
     MNPot<D3<T>> P;
     mn_potentials<T, D3<T>>(c, r, th, P);

@@ -122,7 +122,7 @@ gt_options effective(const gt_options &o)
     gt_options e = o;
     if (e.block_size == 0) e.block_size = 128;
     if (e.blocks_per_sm == 0) e.blocks_per_sm = 4;
-    if (e.reproject_every == 0) e.reproject_every = 256;
+    if (e.reproject_every == 0) e.reproject_every = 4096;
     return e;
 }
 

@@ -353,7 +353,7 @@ __device__ __forceinline__ void park(const TraceArgs &A, int64_t id, uint32_t n,
 }
 
 template <int MODE, int KIND>
-__global__ void __launch_bounds__(256) trace_kernel(TraceArgs A, int one_shot)
+__device__ __forceinline__ void trace_body(const TraceArgs &A, int one_shot)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -627,6 +627,12 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs A, int one_shot)
             active = false;
         }
     }
+}
+
+template <int MODE, int KIND>
+__global__ void __launch_bounds__(256) trace_kernel(TraceArgs A, int one_shot)
+{
+    trace_body<MODE, KIND>(A, one_shot);
 }
 
 // Loop condition of the graph-resident FP32-mixed rounds: continue while rays are parked.

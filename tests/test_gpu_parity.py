@@ -264,6 +264,22 @@ def test_mixed_terminating_classification_and_angle(tracer, oracle, cam, n_steps
     assert rep["agree"] >= 0.999 and rep["max_angle_escaped"] <= 1e-3, rep
 
 
+def test_mixed_reprojection_interval(tracer, oracle):
+    """H = 0 re-projection of p_r (FP64, every K steps): with K = 16 (re-projecting
+    hundreds of times per ray) and with K beyond the step cap (never), the mixed path
+    meets the same classification and angle criteria; the two runs differ, so the
+    re-projection ran."""
+    cam = KERR
+    ref = run_oracle(oracle, cam, 500000, 1.5e-4, want_min_sin=True)
+    band = neighbour_band(ref["status"], cam.res_x, cam.res_y) | (ref["min_sin"] < 1e-3)
+    outs = {}
+    for k in (16, 1 << 30):
+        outs[k] = run_gpu(tracer, cam, 500000, 1.5e-4, mode=1, reproject_every=k)
+        rep = mixed_report(outs[k], ref, exclude=band)
+        assert rep["agree"] >= 0.999 and rep["max_angle_escaped"] <= 1e-3, (k, rep)
+    assert not np.array_equal(outs[16]["th"], outs[1 << 30]["th"])
+
+
 def test_mixed_full_size_sampled(tracer, oracle):
     """The benchmark launch: 1000x1000 Manko-Novikov, 20,000 steps, FP32-mixed, against
     the oracle on 64 sampled pixels."""

@@ -434,8 +434,9 @@ cudaError_t gemm(const void *A, int64_t a_sm, int64_t a_sk, const void *B, int64
     g.C16T = C16T;
     g.ldt = M;
     g.err = err;
-    // 128-wide tiles: two CTAs fit per SM (3 stages x 32 KB of operands each)
-    const int bn = N >= 128 ? 128 : (N >= 64 ? 64 : (N >= 32 ? 32 : 16));
+    // 256-wide tiles read each A row block once when there are many of them (inference
+    // chunks); 128-wide ones give a training batch twice as many tiles to spread over SMs
+    const int bn = (N >= 256 && M >= 65536) ? 256 : N >= 128 ? 128 : (N >= 64 ? 64 : (N >= 32 ? 32 : 16));
     return launch_gemm(g, bn, splits, st);
 }
 

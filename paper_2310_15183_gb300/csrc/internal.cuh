@@ -78,6 +78,9 @@ struct TraceArgs {
     int64_t n_steps;
     double sp;        // step_precision
     double w6;        // RK4 weight (1/6, or 0.1667 in compat mode)
+    // float copies for the FP32 kernel, filled by launch_trace (kernel parameters the
+    // loop reads directly, so no per-step conversions are rematerialised)
+    float sp_f, w6_f, h_thr_f;
     int flags;
     int reproject_every;
     uint64_t timeout_ns; // 0 = no watchdog

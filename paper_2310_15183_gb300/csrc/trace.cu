@@ -370,14 +370,15 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A, int one_shot)
     bool active = false;
     bool drained = false;
     uint32_t n = 0;
+    uint32_t rp_next = 0xFFFFFFFFu; // next step count that is a multiple of reproject_every
     Ray64 x;
     RayMixed m;
     SpacetimeC st = cams[0].st;
     SpacetimeF stf = to_float(st);
     double r_esc = cams[0].r_escape;
     double r_sw = cams[0].r_switch;
-    const float spf = (float)A.sp, w6f = (float)A.w6;
-    const float h_thr_f = (float)(A.sp * 0.00003);
+    const float spf = A.sp_f, w6f = A.w6_f;
+    const float h_thr_f = A.h_thr_f;
     F2 r_esc_f = f2_from(r_esc);
     float r_sw_f = (float)r_sw;
 
@@ -455,7 +456,14 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A, int one_shot)
             x.pt = it.pt;
             x.pph = it.pph;
         }
-        if (MODE == 1 || MODE == 2) mixed_from64(x, m);
+        if (MODE == 1 || MODE == 2) {
+            mixed_from64(x, m);
+            if (A.reproject_every > 0) {
+                const uint64_t k = (uint64_t)A.reproject_every;
+                const uint64_t nx = ((uint64_t)n / k + 1u) * k;
+                rp_next = nx < 0xFFFFFFFFull ? (uint32_t)nx : 0xFFFFFFFFu;
+            }
+        }
         return true;
     };
 
@@ -572,7 +580,10 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A, int one_shot)
                 status = exit_status(r_now, h, r_esc, A.sp, n, A.n_steps);
                 if (status >= 0) {
                     mixed_to64(m, x);
-                } else if (A.reproject_every > 0 && (n % (uint32_t)A.reproject_every) == 0u) {
+                } else if (n == rp_next) {
+                    rp_next = rp_next + (uint32_t)A.reproject_every < rp_next
+                                  ? 0xFFFFFFFFu
+                                  : rp_next + (uint32_t)A.reproject_every;
                     mixed_to64(m, x);
                     reproject_pr(st, x);
                     m.pr = f2_from(x.pr);
@@ -599,7 +610,10 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A, int one_shot)
                 bool parked;
                 park(A, id, n, cam, x, &parked);
                 if (parked) active = false;
-            } else if (A.reproject_every > 0 && (n % (uint32_t)A.reproject_every) == 0u) {
+            } else if (n == rp_next) {
+                rp_next = rp_next + (uint32_t)A.reproject_every < rp_next
+                              ? 0xFFFFFFFFu
+                              : rp_next + (uint32_t)A.reproject_every;
                 mixed_to64(m, x);
                 SpacetimeC st64;
                 if (A.rays) {
@@ -665,9 +679,13 @@ static cudaError_t launch_mode(const TraceArgs &a, int kind_hint, int block, int
     return launch_one<MODE, 2>(a, block, grid, one_shot, s);
 }
 
-cudaError_t launch_trace(const TraceArgs &a, int kmode, int kind_hint, int block, int grid,
+cudaError_t launch_trace(const TraceArgs &args, int kmode, int kind_hint, int block, int grid,
                          bool one_shot, cudaStream_t s)
 {
+    TraceArgs a = args;
+    a.sp_f = (float)a.sp;
+    a.w6_f = (float)a.w6;
+    a.h_thr_f = (float)(a.sp * 0.00003);
     switch (kmode) {
     case KMODE_FP64: return launch_mode<0>(a, kind_hint, block, grid, one_shot, s);
     case KMODE_MIXED_INLINE: return launch_mode<1>(a, kind_hint, block, grid, one_shot, s);

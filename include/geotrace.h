@@ -81,7 +81,8 @@ typedef struct gt_options {
     int blocks_per_sm;       /* persistent grid = min(blocks_per_sm, resident limit) * SMs; 0 = 4 */
     int flags;               /* GT_FLAG_* */
     int reproject_every;     /* FP32-mixed: steps between H = 0 re-projections; 0 = 4096 */
-    double r_switch;         /* FP32-mixed: FP64 zone r < r_switch; 0 = automatic, < 0 = none */
+    double r_switch;         /* FP32-mixed: FP64 zone r < r_switch; < 0 = none; 0 = automatic:
+                                none for Kerr, 4M for Manko-Novikov */
     double timeout_seconds;  /* device watchdog (wall clock per launch); 0 = none */
 } gt_options;
 

@@ -255,9 +255,13 @@ def test_mixed_literal_mn(tracer, oracle):
     assert rep["agree"] == 1.0 and rep["max_angle"] < 1e-4, rep
 
 
-@pytest.mark.parametrize("cam,n_steps", [(W.sub_camera(SCHW, 24, 20), 400000), (KERR, 500000)])
-def test_mixed_terminating_classification_and_angle(tracer, oracle, cam, n_steps):
-    got = run_gpu(tracer, cam, n_steps, 1.5e-4, mode=1)
+@pytest.mark.parametrize("cam,n_steps,r_switch", [(W.sub_camera(SCHW, 24, 20), 400000, 0.0),
+                                                  (KERR, 500000, 0.0), (KERR, 500000, 1.5),
+                                                  (W.sub_camera(MN, 12, 10), 500000, 0.0)])
+def test_mixed_terminating_classification_and_angle(tracer, oracle, cam, n_steps, r_switch):
+    """Terminating rays, FP32-mixed against the oracle: Kerr without FP64 zone (the
+    default), Kerr with one, and Manko-Novikov with its default 4M zone."""
+    got = run_gpu(tracer, cam, n_steps, 1.5e-4, mode=1, r_switch=r_switch)
     ref = run_oracle(oracle, cam, n_steps, 1.5e-4, want_min_sin=True)
     band = neighbour_band(ref["status"], cam.res_x, cam.res_y) | (ref["min_sin"] < 1e-3)
     rep = mixed_report(got, ref, exclude=band)
@@ -319,7 +323,8 @@ def test_graph_launch_replays_the_batch(g, tracer, oracle):
             W.Camera(0.5, 0.24, 0.0, 15.0, 80 * W.DEG, 30.0, 12, 10)]
     tracer.set_options()
     direct = to_numpy(tracer.trace_batch(cams, 300000, 1.5e-4, 0))
-    tracer.set_options(flags=g.FLAG_GRAPH)
+    # an explicit FP64 zone (Kerr has none by default) so that rays park and resume
+    tracer.set_options(flags=g.FLAG_GRAPH, r_switch=1.5)
     out = tracer.alloc_outputs(sum(c.n_rays for c in cams))
     for _ in range(2):
         for v in out.values():
@@ -330,7 +335,7 @@ def test_graph_launch_replays_the_batch(g, tracer, oracle):
             assert np.array_equal(got[key], direct[key]), key
     mixed = to_numpy(tracer.trace_batch(cams, 300000, 1.5e-4, 1))
     torch.cuda.synchronize()
-    tracer.set_options()
+    tracer.set_options(r_switch=1.5)
     rounds = to_numpy(tracer.trace_batch(cams, 300000, 1.5e-4, 1))
     torch.cuda.synchronize()
     for key in ("t", "r", "th", "ph", "status", "nsteps"):  # same kernels, same bits
@@ -351,7 +356,8 @@ def test_pixel_list_trace_matches_full_image(tracer):
     cam = W.sub_camera(W.SCHW_64, 40, 30)
     pix = W.sample_pixels(cam.n_rays, 173, seed=9)
     for mode, n_steps in ((0, 400000), (1, 400000)):
-        full = run_gpu(tracer, cam, n_steps, 1.5e-4, mode=mode)
+        # explicit FP64 zone: mixed rays park and resume (Kerr has none by default)
+        full = run_gpu(tracer, cam, n_steps, 1.5e-4, mode=mode, r_switch=1.5)
         sub = to_numpy(tracer.trace_pixels(torch.tensor(pix, device="cuda"), n_steps, 1.5e-4, mode))
         torch.cuda.synchronize()
         for k in ("t", "r", "th", "ph", "status", "nsteps"):

@@ -294,7 +294,8 @@ int gt_measure_fma_peak(int device, int fp64, int iters, double *flops_per_s);
 
 /* BF16 tensor-core GEMM on `device` / `cuda_stream` (tcgen05, FP32 accumulation in
  * tensor memory), the building block of the surrogate network's training and
- * inference: C[m, n] (+)= act(sum_k A[m, k] B[n, k] + bias[n]) for m < M, n < N.
+ * inference (which also runs it on FP16 operands internally):
+ * C[m, n] (+)= act(sum_k A[m, k] B[n, k] + bias[n]) for m < M, n < N.
  * A (m, k) is read at A[m * a_sm + k * a_sk] and B (n, k) at B[n * b_sn + k * b_sk]
  * (bf16 device arrays, any strides, so transposed views need no copy); bias is an
  * optional float32[N]; act 0 = identity, 1 = SiLU; C is float32 row-major with

@@ -1,14 +1,22 @@
-// mlp.cu -- BF16 tensor-core GEMM on tcgen05 (TMEM accumulators) and the small
-// elementwise kernels of the surrogate network's forward and backward passes.
+// mlp.cu -- tensor-core GEMM on tcgen05 (TMEM accumulators) for the surrogate network's
+// forward and backward passes.
 //
 // gemm:  C[m, n] = sum_k A[m, k] B[n, k]  (+ bias[n]) (then SiLU)
 //   A element (m, k) at A[m * a_sm + k * a_sk], B element (n, k) at B[n * b_sn + k * b_sk]
-//   (bf16; any strides, so transposed operands need no copy), FP32 accumulation in
-//   TMEM.  One CTA of 128 threads owns a 128 x BN output tile; K runs in chunks of
-//   64 through two shared-memory stages: all threads stage a chunk (16-byte vector
-//   loads when K is contiguous), one thread issues four 128 x BN x 16 MMAs and
-//   commits them to the stage's mbarrier, which the stage's next writer waits on.
-//   Split-K over gridDim.z accumulates into C with atomics.
+//   (bf16, or fp16 for both; any strides, so transposed operands need no copy), FP32
+//   accumulation in TMEM; outputs any of: FP32 C (stored, or added for split-K), the FP32
+//   pre-activation, a 16-bit copy and a transposed bf16 copy.
+//
+// Three kernels, chosen by operand layout:
+//  * tc_gemm_ws_kernel (K-contiguous operands with encodable TMA tensor maps): persistent,
+//    one CTA per SM walking (n, m, k-split) tiles; warp 0 loads A and B chunks with TMA
+//    into S stages (mbarrier complete_tx), warp 1 issues the MMAs into one of two TMEM
+//    accumulators, eight epilogue warps drain the other one -- bias, SiLU, swizzled
+//    shared-memory boxes written back by TMA bulk tensor stores (FP32 add-reductions
+//    for split-K) -- so loads, MMAs and stores of consecutive tiles overlap.
+//  * tc_gemm_pipe_kernel (K-contiguous, no tensor map): one CTA per 128 x BN tile, a
+//    three-stage cp.async pipeline, the MMA thread committing each stage to its mbarrier.
+//  * tc_gemm_kernel (any strides): the same tile with register-staged loads.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>

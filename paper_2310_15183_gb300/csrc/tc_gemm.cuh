@@ -1,6 +1,7 @@
 // tc_gemm.cuh -- fifth-generation tensor-core (tcgen05) building blocks for sm_103a:
 // TMEM allocation, UMMA shared-memory / instruction descriptors, kind::f16 MMA with
-// BF16 operands and FP32 accumulation in TMEM, commit to an mbarrier, TMEM loads.
+// BF16 or FP16 operands and FP32 accumulation in TMEM, commit to an mbarrier, TMEM
+// loads, and the TMA bulk-tensor loads, stores and reductions with their mbarriers.
 //
 // Operand layout in shared memory: K-major, no swizzle, 8x8 "core matrices" of
 // 8 rows x 16 bytes.  Core matrix (g, kb) -- row group g = row/8, column block

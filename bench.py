@@ -297,14 +297,15 @@ def leg_surrogate(tr, geotrace, args, torch):
                 "angle_err_median": float(np.median(ang)) if ang.size else 0.0}
 
     res["fp32_mixed_vs_fp64"] = accuracy(md)
-    for tau, band in ((2.0, 0.02), (4.0, 0.05)):
+    for tau, band, dtol in ((2.0, 0.02, 0.0), (4.0, 0.05, 0.0), (2.0, 0.02, 0.005)):
         out = tr.alloc_outputs(cam.n_rays)
         (out, nfb), t_inf = _timed(torch, tr.stream,
                                    lambda: sg.infer(tr, tau, band, cap, sp,
-                                                    geotrace.MODE_FP32_MIXED, out=out))
+                                                    geotrace.MODE_FP32_MIXED, out=out,
+                                                    dir_tol=dtol))
         got = {k: out[k][torch.tensor(judge_pix, device="cuda")].cpu().numpy()
                for k in ("status", "th", "ph")}
-        res[f"tau{tau}_band{band}"] = {
+        res[f"tau{tau}_band{band}" + (f"_dirtol{dtol}" if dtol else "")] = {
             "seconds": t_inf, "fallback_pixels": nfb, "fallback_frac": nfb / cam.n_rays,
             "speedup_vs_integrator_only": integ_full_s / t_inf, **accuracy(got)}
     res["integrator_only_seconds_extrapolated"] = integ_full_s

@@ -231,15 +231,20 @@ int gt_surrogate_train(gt_ctx *ctx, gt_surrogate *s, const gt_train_cfg *cfg, in
 
 /* Image of the configured camera through the surrogate: pixels with |logit| >= tau that
  * are not in the photon-ring band (Kerr: |min_r R(r)/(E^2 r^4)| < band from the pixel's
- * constants of motion; band = 0 disables) take the network's answer -- status ESCAPED
- * with end theta, phi from the predicted direction, or HORIZON with NaN angles; t and r
- * are NaN and nsteps 0 for them.  All other pixels are traced by the integrator (mode,
- * n_steps, step_precision as gt_trace) and written in place.  Outputs as gt_trace
- * (device, res_x*res_y each, none may be NULL); *n_fallback receives the number of
- * integrated pixels.  Synchronous. */
-int gt_surrogate_infer(gt_ctx *ctx, gt_surrogate *s, float tau, double band, int64_t n_steps,
-                       double step_precision, int mode, double *t, double *r, double *theta,
-                       double *phi, uint8_t *status, uint32_t *nsteps, int64_t *n_fallback);
+ * constants of motion; band = 0 disables) and, when predicted to escape, whose predicted
+ * direction vector has a length within dir_tol of 1 (dir_tol = 0 disables; the network
+ * is trained on unit vectors, and a shorter or longer one marks a region where it has not
+ * settled) take the network's answer -- status ESCAPED with end theta, phi from the
+ * predicted direction, or HORIZON with NaN angles; t and r are NaN and nsteps 0 for
+ * them.  All other pixels are traced by the integrator (mode, n_steps, step_precision as
+ * gt_trace) and written in place.  Outputs as gt_trace (device, res_x*res_y each, none
+ * may be NULL); *n_fallback receives the number of integrated pixels.  Errors:
+ * GT_ERR_INVALID_ARG (negative tau, band or dir_tol, NULL pointers) and those of
+ * gt_trace.  Synchronous. */
+int gt_surrogate_infer(gt_ctx *ctx, gt_surrogate *s, float tau, double band, float dir_tol,
+                       int64_t n_steps, double step_precision, int mode, double *t, double *r,
+                       double *theta, double *phi, uint8_t *status, uint32_t *nsteps,
+                       int64_t *n_fallback);
 
 /* Largest batch gt_trace_batch_noalloc accepts. */
 #define GT_NOALLOC_MAX_CAMS 64

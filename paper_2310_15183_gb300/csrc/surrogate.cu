@@ -244,8 +244,8 @@ __device__ double kerr_rmin(const CamDesc &c, const Ray64 &p)
 
 // Decide per pixel: confident surrogate answer, or fall back to the integrator.
 __global__ void gate_kernel(int64_t n, int64_t pix0, const CamDesc *cam, const float *Z5, float tau,
-                            double band, double *t, double *r, double *th, double *ph,
-                            uint8_t *status, uint32_t *nsteps, int64_t *fallback,
+                            double band, float dir_tol, double *t, double *r, double *th,
+                            double *ph, uint8_t *status, uint32_t *nsteps, int64_t *fallback,
                             unsigned long long *n_fallback)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -260,11 +260,13 @@ __global__ void gate_kernel(int64_t n, int64_t pix0, const CamDesc *cam, const f
             camera_init(*cam, pix, p);
             ring = fabs(kerr_rmin(*cam, p)) < band;
         }
-        fb = fabsf(logit) < tau || ring;
+        const float nx = z[1], ny = z[2], nz = z[3];
+        const float nn = sqrtf(nx * nx + ny * ny + nz * nz);
+        // an escaping prediction whose direction vector is not of unit length is unsettled
+        const bool loose = dir_tol > 0.0f && logit > 0.0f && !(fabsf(nn - 1.0f) <= dir_tol);
+        fb = fabsf(logit) < tau || ring || loose;
         if (!fb) {
             if (logit > 0.0f) {
-                const float nx = z[1], ny = z[2], nz = z[3];
-                const float nn = sqrtf(nx * nx + ny * ny + nz * nz);
                 th[pix] = acos(fminf(fmaxf(nz / nn, -1.0f), 1.0f));
                 ph[pix] = atan2(ny, nx);
                 status[pix] = GT_RAY_ESCAPED;
@@ -736,8 +738,8 @@ namespace gt {
 namespace sg {
 
 int infer_chunks(gt_surrogate *s, const CamDesc *d_cam, int64_t n_pix, float tau, double band,
-                 double *t, double *r, double *th, double *ph, uint8_t *status, uint32_t *nsteps,
-                 int64_t *d_fallback, unsigned long long *d_nfb, cudaStream_t st)
+                 float dir_tol, double *t, double *r, double *th, double *ph, uint8_t *status,
+                 uint32_t *nsteps, int64_t *d_fallback, unsigned long long *d_nfb, cudaStream_t st)
 {
     const int64_t chunk = 1 << 19;
     int rc = ensure_ws(s, n_pix < chunk ? n_pix : chunk);
@@ -747,8 +749,9 @@ int infer_chunks(gt_surrogate *s, const CamDesc *d_cam, int64_t n_pix, float tau
         camera_features_kernel<<<blocks_for(B), 256, 0, st>>>(B, p0, d_cam, s->norm, s->X[0]);
         cudaError_t e = forward(s, (int)B, st, false);
         if (e != cudaSuccess) return GT_ERR_CUDA;
-        gate_kernel<<<blocks_for(B), 256, 0, st>>>(B, p0, d_cam, s->Z[N_LAYERS - 1], tau, band, t, r,
-                                                   th, ph, status, nsteps, d_fallback, d_nfb);
+        gate_kernel<<<blocks_for(B), 256, 0, st>>>(B, p0, d_cam, s->Z[N_LAYERS - 1], tau, band,
+                                                   dir_tol, t, r, th, ph, status, nsteps,
+                                                   d_fallback, d_nfb);
         if (cudaGetLastError() != cudaSuccess) return GT_ERR_CUDA;
     }
     return check_err(s, st);

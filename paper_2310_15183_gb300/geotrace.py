@@ -106,7 +106,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.gt_surrogate_eval.argtypes = [vp, vp, i64] + [vp] * 5 + [vp]
     lib.gt_surrogate_grad.argtypes = [vp, vp, i64] + [vp] * 8 + [ctypes.c_float, vp, vp]
     lib.gt_surrogate_train.argtypes = [vp, vp, ctypes.POINTER(TrainCfg), i64] + [vp] * 8 + [vp]
-    lib.gt_surrogate_infer.argtypes = [vp, vp, ctypes.c_float, d, i64, d, i] + out6 + [
+    lib.gt_surrogate_infer.argtypes = [vp, vp, ctypes.c_float, d, ctypes.c_float, i64, d, i] + out6 + [
         ctypes.POINTER(i64)]
     lib.gt_strerror.argtypes = [i]
     lib.gt_strerror.restype = ctypes.c_char_p
@@ -356,13 +356,15 @@ class Surrogate:
         return losses
 
     def infer(self, tracer: "Tracer", tau: float, band: float, n_steps: int,
-              step_precision: float, mode: int = MODE_FP32_MIXED, out: Optional[dict] = None):
+              step_precision: float, mode: int = MODE_FP32_MIXED, out: Optional[dict] = None,
+              dir_tol: float = 0.0):
         n = tracer.res[0] * tracer.res[1]
         if out is None:
             out = tracer.alloc_outputs(n)
         nfb = ctypes.c_int64()
         _check(self.lib.gt_surrogate_infer(tracer.ctx, self.h, float(tau), float(band),
-                                           int(n_steps), float(step_precision), int(mode),
+                                           float(dir_tol), int(n_steps), float(step_precision),
+                                           int(mode),
                                            *[_ptr(out[k]) for k in ("t", "r", "th", "ph",
                                                                     "status", "nsteps")],
                                            ctypes.byref(nfb)), "gt_surrogate_infer")

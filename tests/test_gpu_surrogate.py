@@ -119,5 +119,16 @@ def test_train_on_traced_rays_and_gated_inference(g, tracer, oracle):
         # a 2^15-ray training set only checks the pipeline; the benchmark's surrogate leg
         # measures the accuracy reached with the full 2^22-ray training set
         assert np.median(ang) < 0.2, np.median(ang)
+        # direction-length gate: more pixels fall back, the integrator covers exactly the
+        # pixels the network no longer decides, and the rest are unchanged
+        out2, nfb2 = s.infer(tracer, tau=2.0, band=0.05, n_steps=500000, step_precision=1.5e-4,
+                             dir_tol=0.01)
+        got2 = to_numpy(out2)
+        net2 = got2["nsteps"] == 0
+        assert nfb2 > nfb and not np.any(net2 & ~net)
+        for k in ("status", "th", "ph"):
+            assert np.array_equal(got2[k][net2], got[k][net2], equal_nan=True), k
+        mixed = to_numpy(tracer.trace(500000, 1.5e-4, g.MODE_FP32_MIXED))
+        assert np.array_equal(got2["status"][~net2], mixed["status"][~net2])
     finally:
         s.close()

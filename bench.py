@@ -99,15 +99,16 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ ncu traffic record
+# sources that define the ray-tracing kernels (a traffic record stays valid while they do)
+TRACE_SOURCES = ("trace.cu", "spacetime.cuh", "internal.cuh", "camera.cuh")
+
+
 def source_sha1() -> str:
-    """Hash of the CUDA sources and the C ABI header (identifies the kernel build)."""
-    import glob
+    """Hash of the CUDA sources of the ray-tracing kernels."""
     import hashlib
     h = hashlib.sha1()
-    files = sorted(glob.glob(os.path.join(ROOT, "paper_2310_15183_gb300", "csrc", "*.cu*")) +
-                   glob.glob(os.path.join(ROOT, "include", "*.h")))
-    for f in files:
-        h.update(open(f, "rb").read())
+    for name in TRACE_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2310_15183_gb300", "csrc", name), "rb").read())
     return h.hexdigest()
 
 

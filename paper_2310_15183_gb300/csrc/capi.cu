@@ -570,7 +570,7 @@ int gt_set_options(gt_ctx *c, const gt_options *o)
     if (!isfinite(v.r_switch) || !(v.timeout_seconds >= 0.0) || !isfinite(v.timeout_seconds))
         return GT_ERR_INVALID_ARG;
     if (v.flags & ~(GT_FLAG_COMPAT_WEIGHTS | GT_FLAG_COMPAT_CAMERA | GT_FLAG_ONE_SHOT |
-                    GT_FLAG_GRAPH))
+                    GT_FLAG_GRAPH | GT_FLAG_PRECISE_MN))
         return GT_ERR_INVALID_ARG;
     c->opts = v;
     return GT_OK;

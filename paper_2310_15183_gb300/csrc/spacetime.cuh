@@ -308,7 +308,7 @@ GT_HD void mn_potentials(const SpacetimeT<T> &c, T r, T th, MNPot<N> &P)
 // rounding like the dual-number form below (mn_rates_fwd), with less than half its
 // arithmetic: a product costs one multiply forward and two fused multiply-adds backward
 // instead of five operations for a value and two derivatives.
-template <class T>
+template <class T, bool TAIL = false>
 GT_HD void mn_rates(const SpacetimeT<T> &c, T r, T th, T pr, T pth, T pt, T pph,
                     Rates<T> &o)
 {
@@ -331,17 +331,59 @@ GT_HD void mn_rates(const SpacetimeT<T> &c, T r, T th, T pr, T pth, T pt, T pph,
     const T P3 = u * q3;
     const T iR2 = iR * iR;
     const T iR3 = iR2 * iR;
-    const T uR2 = u * iR2;
     const T P2R3 = P2 * iR3;
-    const T T1 = iR + uR2 + P2R3;
-    const T T2 = uR2 - iR - P2R3;
     const T xmy = x - y, xpy = x + y;
-    const T Sa = xmy * T1;
-    const T Sb = xpy * T2;
-    const T iRP = iR + P2R3;
-    const T Sg = T(2) * (x * iRP - y * uR2);
-    const T fa = exp_t((Sa - T(1)) * (-tb)) * (-al);
-    const T fb = exp_t((Sb + T(1)) * tb) * al;
+    // Ea = Sa - 1, Eb = Sb + 1, Eg = Sg - 2, where Sa, Sb, Sg are the l <= 2 multipole
+    // sums of the metric (Sa = (x - y) sum_l P_l(u)/R^(l+1), Sb = -(x + y) sum_l (-1)^l
+    // P_l(u)/R^(l+1), Sg = Sa - Sb).  The full series sum to 1/(x - y) and 1/(x + y) (the
+    // Legendre generating function with t = 1/R, u R = x y), so Ea and Eb are series tails,
+    // small far out, and the direct differences lose about 2 beta ulp(1) in the exponents.
+    // TAIL (FP32 kernels on request) writes the tails in closed form, without cancellation:
+    //   Ea = -t^3 N(t) / (1 + sa Q(t)),  sa = (x - y) t,  Q(t) = 1 + u t + P2 t^2,
+    //   Eb = -t^3 N(-t) / (1 + sb Q(-t)), sb = (x + y) t,
+    //   N(t) = 2 P3 - c4 t - c5 t^2 - c6 t^3,
+    //   c4 = P2^2 - 4 u^2 P2 + 2 P2 + u^2,  c5 = 2 u P2 (1 - P2),  c6 = P2^2,
+    //   Eg = Ea - Eb;
+    // at the price of ~45 more operations per evaluation.  FP64 keeps the direct
+    // differences (their error there is ~1e-12), and so does the default FP32 path, whose
+    // end states stay within the mixed-precision criteria regardless.
+    T Ea, Eb, Eg;
+    T uR2 = T(0), T1 = T(0), T2 = T(0), iRP = T(0);           // direct form
+    T c4 = T(0), c5 = T(0), c6 = T(0), tw1 = T(0), tw2 = T(0);  // tail form
+    T tv1 = T(0), tv2 = T(0), Nn = T(0), Np = T(0), sa = T(0), sb = T(0);
+    T q1 = T(0), q2 = T(0), Qa = T(0), Qb = T(0), ia = T(0), ib = T(0);
+    if constexpr (TAIL) {
+        c4 = fma_t(P2, P2 - T(4) * u2 + T(2), u2);
+        c5 = T(2) * u * (P2 - P2 * P2);
+        c6 = P2 * P2;
+        tw1 = fma_t(iR, c6, c5);  // c5 + t c6
+        tw2 = fma_t(iR, tw1, c4); // c4 + t tw1
+        Nn = fma_t(-iR, tw2, T(2) * P3);
+        tv1 = fma_t(-iR, c6, c5); // c5 - t c6
+        tv2 = fma_t(-iR, tv1, c4); // c4 - t tv1
+        Np = fma_t(iR, tv2, T(2) * P3);
+        sa = xmy * iR;
+        sb = xpy * iR;
+        q1 = fma_t(P2, iR, u);   // u + P2 t
+        q2 = fma_t(-P2, iR, u);  // u - P2 t
+        Qa = fma_t(iR, q1, T(1));
+        Qb = fma_t(-iR, q2, T(1));
+        ia = rcp_t(fma_t(sa, Qa, T(1)));
+        ib = rcp_t(fma_t(sb, Qb, T(1)));
+        Ea = -iR3 * Nn * ia;
+        Eb = -iR3 * Np * ib;
+        Eg = Ea - Eb;
+    } else {
+        uR2 = u * iR2;
+        T1 = iR + uR2 + P2R3;
+        T2 = uR2 - iR - P2R3;
+        iRP = iR + P2R3;
+        Ea = xmy * T1 - T(1);
+        Eb = xpy * T2 + T(1);
+        Eg = T(2) * (x * iRP - y * uR2) - T(2);
+    }
+    const T fa = exp_t(Ea * (-tb)) * (-al);
+    const T fb = exp_t(Eb * tb) * al;
     const T ab = fa * fb;
     const T opab = ab + T(1);
     const T bma = fb - fa;
@@ -358,7 +400,7 @@ GT_HD void mn_rates(const SpacetimeT<T> &c, T r, T th, T pr, T pth, T pt, T pph,
     const T psi2 = tb * P2R3;
     const T D = P3 * P3 - P2 * P2;
     const T t3 = T(c.three_beta2) * (iR3 * iR3);
-    const T g2 = fma_t(t3, D, (Sg - T(2)) * tb);
+    const T g2 = fma_t(t3, D, Eg * tb);
     const T e2psi = exp_t(psi2);
     const T ie2psi = rcp_t(e2psi);
     const T iA = rcp_t(A);
@@ -426,7 +468,7 @@ GT_HD void mn_rates(const SpacetimeT<T> &c, T r, T th, T pr, T pth, T pt, T pph,
     // g2 = t3 D + tb (Sg - 2), t3 = 3 beta^2 iR3^2
     const T D_b = g2_b * t3;
     T iR3_b = g2_b * D * T(c.three_beta2) * T(2) * iR3;
-    const T Sg_b = g2_b * tb;
+    const T Eg_b = g2_b * tb;
     T P3_b = T(2) * P3 * D_b;
     T P2_b = T(-2) * P2 * D_b;
     T P2R3_b = tb * psi2_b;
@@ -461,30 +503,69 @@ GT_HD void mn_rates(const SpacetimeT<T> &c, T r, T th, T pr, T pth, T pt, T pph,
     ab_b = ab_b + opab_b;
     fa_b = fma_t(ab_b, fb, fa_b);
     fb_b = fma_t(ab_b, fa, fb_b);
-    // fa = -alpha exp(-2 beta (Sa - 1)), fb = alpha exp(2 beta (Sb + 1))
-    const T Sa_b = -fa_b * fa * tb;
-    const T Sb_b = fb_b * fb * tb;
-    // Sg = 2 (x (iR + P2R3) - y uR2)
-    const T Sg2 = T(2) * Sg_b;
-    x_b = fma_t(Sg2, iRP, x_b);
-    T iR_b = Sg2 * x;
-    P2R3_b = fma_t(Sg2, x, P2R3_b);
-    y_b = fma_t(-Sg2, uR2, y_b);
-    T uR2_b = -Sg2 * y;
-    // Sa = (x - y) T1, Sb = (x + y) T2
-    x_b = x_b + Sa_b * T1 + Sb_b * T2;
-    y_b = y_b - Sa_b * T1 + Sb_b * T2;
-    const T T1_b = Sa_b * xmy, T2_b = Sb_b * xpy;
-    iR_b = iR_b + T1_b - T2_b;
-    uR2_b = uR2_b + T1_b + T2_b;
-    P2R3_b = P2R3_b + T1_b - T2_b;
-    // P2R3 = P2 iR3, uR2 = u iR2, iR3 = iR2 iR, iR2 = iR^2
-    P2_b = fma_t(P2R3_b, iR3, P2_b);
-    iR3_b = fma_t(P2R3_b, P2, iR3_b);
-    T u_b = uR2_b * iR2;
-    T iR2_b = fma_t(uR2_b, u, iR3_b * iR);
-    iR_b = fma_t(iR3_b, iR2, iR_b);
-    iR_b = fma_t(T(2) * iR, iR2_b, iR_b);
+    // fa = -alpha exp(-2 beta Ea), fb = alpha exp(2 beta Eb)
+    T Ea_b = -fa_b * fa * tb;
+    T Eb_b = fb_b * fb * tb;
+    T iR_b, u_b, iR2_b;
+    if constexpr (TAIL) {
+        // Eg = Ea - Eb
+        Ea_b = Ea_b + Eg_b;
+        Eb_b = Eb_b - Eg_b;
+        // Ea = -iR3 Nn ia, ia = 1 / (1 + sa Qa); Eb likewise
+        iR3_b = iR3_b - (Nn * ia * Ea_b + Np * ib * Eb_b);
+        const T Nn_b = -iR3 * ia * Ea_b, Np_b = -iR3 * ib * Eb_b;
+        const T Da_b = -Ea * ia * Ea_b, Db_b = -Eb * ib * Eb_b;
+        const T sa_b = Da_b * Qa, Qa_b = Da_b * sa;
+        const T sb_b = Db_b * Qb, Qb_b = Db_b * sb;
+        // sa = (x - y) t, sb = (x + y) t, t = iR
+        x_b = fma_t(iR, sa_b + sb_b, x_b);
+        y_b = fma_t(iR, sb_b - sa_b, y_b);
+        iR_b = fma_t(xmy, sa_b, xpy * sb_b);
+        // Qa = 1 + t q1, q1 = u + P2 t;  Qb = 1 - t q2, q2 = u - P2 t
+        const T q1_b = iR * Qa_b, q2_b = -iR * Qb_b;
+        iR_b = iR_b + q1 * Qa_b - q2 * Qb_b + P2 * (q1_b - q2_b);
+        u_b = q1_b + q2_b;
+        P2_b = fma_t(iR, q1_b - q2_b, P2_b);
+        // Nn = 2 P3 - t tw2, tw2 = c4 + t tw1, tw1 = c5 + t c6;
+        // Np = 2 P3 + t tv2, tv2 = c4 - t tv1, tv1 = c5 - t c6
+        P3_b = fma_t(T(2), Nn_b + Np_b, P3_b);
+        const T tw2_b = -iR * Nn_b, tv2_b = iR * Np_b;
+        const T tw1_b = iR * tw2_b, tv1_b = -iR * tv2_b;
+        iR_b = iR_b - tw2 * Nn_b + tv2 * Np_b + tw1 * tw2_b - tv1 * tv2_b + c6 * (tw1_b - tv1_b);
+        const T c4_b = tw2_b + tv2_b, c5_b = tw1_b + tv1_b, c6_b = iR * (tw1_b - tv1_b);
+        // c4 = P2 (P2 - 4 u2 + 2) + u2, c5 = 2 u (P2 - P2^2), c6 = P2^2
+        P2_b = P2_b + c4_b * (T(2) * P2 - T(4) * u2 + T(2)) +
+               c5_b * (T(2) * u) * (T(1) - T(2) * P2) + c6_b * (T(2) * P2);
+        u_b = u_b + c4_b * (T(2) * u - T(8) * u * P2) + c5_b * (T(2) * (P2 - P2 * P2));
+        // P2R3 = P2 iR3 (in psi2), iR3 = iR2 iR, iR2 = iR^2
+        P2_b = fma_t(P2R3_b, iR3, P2_b);
+        iR3_b = fma_t(P2R3_b, P2, iR3_b);
+        iR2_b = iR3_b * iR;
+        iR_b = fma_t(iR3_b, iR2, iR_b);
+        iR_b = fma_t(T(2) * iR, iR2_b, iR_b);
+    } else {
+        // Eg = 2 (x (iR + P2R3) - y uR2) - 2
+        const T Sg2 = T(2) * Eg_b;
+        x_b = fma_t(Sg2, iRP, x_b);
+        iR_b = Sg2 * x;
+        P2R3_b = fma_t(Sg2, x, P2R3_b);
+        y_b = fma_t(-Sg2, uR2, y_b);
+        T uR2_b = -Sg2 * y;
+        // Ea = (x - y) T1 - 1, Eb = (x + y) T2 + 1
+        x_b = x_b + Ea_b * T1 + Eb_b * T2;
+        y_b = y_b - Ea_b * T1 + Eb_b * T2;
+        const T T1_b = Ea_b * xmy, T2_b = Eb_b * xpy;
+        iR_b = iR_b + T1_b - T2_b;
+        uR2_b = uR2_b + T1_b + T2_b;
+        P2R3_b = P2R3_b + T1_b - T2_b;
+        // P2R3 = P2 iR3, uR2 = u iR2, iR3 = iR2 iR, iR2 = iR^2
+        P2_b = fma_t(P2R3_b, iR3, P2_b);
+        iR3_b = fma_t(P2R3_b, P2, iR3_b);
+        u_b = uR2_b * iR2;
+        iR2_b = fma_t(uR2_b, u, iR3_b * iR);
+        iR_b = fma_t(iR3_b, iR2, iR_b);
+        iR_b = fma_t(T(2) * iR, iR2_b, iR_b);
+    }
     // P3 = u q3, q3 = 2.5 u2 - 1.5, P2 = 1.5 u2 - 0.5, u2 = u^2
     u_b = fma_t(P3_b, q3, u_b);
     const T u2_b = P3_b * u * T(2.5) + T(1.5) * P2_b;

@@ -265,34 +265,30 @@ __device__ __forceinline__ void mixed_to64(const RayMixed &m, Ray64 &x)
 #define GT_FIELD_ATTR __forceinline__
 #endif
 
-template <int KIND>
+template <int KIND, bool PRECISE>
 __device__ GT_FIELD_ATTR void rates_f32(const SpacetimeF &st, float r, float th, float pr,
                                           float pth, float pt, float pph, Rates<float> &o)
 {
-    if (KIND == 2) {
-        if (st.kind == KIND_KERR)
-            kerr_rates<float>(st, r, th, pr, pth, pt, pph, o);
-        else
-            mn_rates<float>(st, r, th, pr, pth, pt, pph, o);
-    } else {
-        rates<KIND, float>(st, r, th, pr, pth, pt, pph, o);
-    }
+    if (KIND == KIND_KERR || (KIND == 2 && st.kind == KIND_KERR))
+        kerr_rates<float>(st, r, th, pr, pth, pt, pph, o);
+    else
+        mn_rates<float, PRECISE>(st, r, th, pr, pth, pt, pph, o);
 }
 
 // One FP32 RK4 step on the compensated state; returns h (as float).
-template <int KIND>
+template <int KIND, bool PRECISE = false>
 __device__ __forceinline__ float rk4_step32(const SpacetimeF &st, RayMixed &m, float sp, float w6)
 {
     Rates<float> k1, k2, k3, k4;
     const float r = m.r.hi, th = m.th.hi, pr = m.pr.hi, pth = m.pth.hi;
-    rates_f32<KIND>(st, r, th, pr, pth, m.ptf, m.pphf, k1);
+    rates_f32<KIND, PRECISE>(st, r, th, pr, pth, m.ptf, m.pphf, k1);
     const float h = fabsf(sp / k1.dt);
     const float hh = 0.5f * h;
-    rates_f32<KIND>(st, fmaf(hh, k1.dr, r), fmaf(hh, k1.dth, th), fmaf(hh, k1.dpr, pr),
+    rates_f32<KIND, PRECISE>(st, fmaf(hh, k1.dr, r), fmaf(hh, k1.dth, th), fmaf(hh, k1.dpr, pr),
                     fmaf(hh, k1.dpth, pth), m.ptf, m.pphf, k2);
-    rates_f32<KIND>(st, fmaf(hh, k2.dr, r), fmaf(hh, k2.dth, th), fmaf(hh, k2.dpr, pr),
+    rates_f32<KIND, PRECISE>(st, fmaf(hh, k2.dr, r), fmaf(hh, k2.dth, th), fmaf(hh, k2.dpr, pr),
                     fmaf(hh, k2.dpth, pth), m.ptf, m.pphf, k3);
-    rates_f32<KIND>(st, fmaf(h, k3.dr, r), fmaf(h, k3.dth, th), fmaf(h, k3.dpr, pr),
+    rates_f32<KIND, PRECISE>(st, fmaf(h, k3.dr, r), fmaf(h, k3.dth, th), fmaf(h, k3.dpr, pr),
                     fmaf(h, k3.dpth, pth), m.ptf, m.pphf, k4);
     const float hw = h * w6;
     f2_add(m.t, hw * (k1.dt + 2.0f * k2.dt + 2.0f * k3.dt + k4.dt));
@@ -355,7 +351,7 @@ __device__ __forceinline__ void park(const TraceArgs &A, int64_t id, uint32_t n,
     *ok = true;
 }
 
-template <int MODE, int KIND>
+template <int MODE, int KIND, bool PRECISE>
 __device__ __forceinline__ void trace_body(const TraceArgs &A, int one_shot)
 {
     const int lane = threadIdx.x & 31;
@@ -594,7 +590,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A, int one_shot)
             }
         } else { // MODE 2: FP32 steps only, exit tests in FP32
             RayMixed keep = m;
-            const float h = rk4_step32<KIND>(stf, m, spf, w6f);
+            const float h = rk4_step32<KIND, PRECISE>(stf, m, spf, w6f);
             ++n;
             const bool ok = isfinite(h) && isfinite(m.t.hi) && isfinite(m.r.hi) &&
                             isfinite(m.th.hi) && isfinite(m.ph.hi) && isfinite(m.pr.hi) &&
@@ -646,10 +642,12 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A, int one_shot)
     }
 }
 
-template <int MODE, int KIND>
-__global__ void __launch_bounds__(256) trace_kernel(TraceArgs A, int one_shot)
+// The FP32 rounds kernel (MODE 2) is held to 128 registers: four resident blocks of 128
+// threads per SM, also with PRECISE (GT_FLAG_PRECISE_MN), which needs a few more.
+template <int MODE, int KIND, bool PRECISE = false>
+__global__ void __launch_bounds__(256, MODE == 2 ? 2 : 1) trace_kernel(TraceArgs A, int one_shot)
 {
-    trace_body<MODE, KIND>(A, one_shot);
+    trace_body<MODE, KIND, PRECISE>(A, one_shot);
 }
 
 // Loop condition of the graph-resident FP32-mixed rounds: continue while rays are parked.
@@ -669,6 +667,12 @@ cudaError_t launch_set_condition(cudaGraphConditionalHandle h, const unsigned lo
 template <int MODE, int KIND>
 static cudaError_t launch_one(const TraceArgs &a, int block, int grid, bool one_shot, cudaStream_t s)
 {
+    if constexpr (MODE == 2 && KIND != KIND_KERR) {
+        if (a.flags & GT_FLAG_PRECISE_MN) {
+            trace_kernel<MODE, KIND, true><<<grid, block, 0, s>>>(a, one_shot ? 1 : 0);
+            return cudaGetLastError();
+        }
+    }
     trace_kernel<MODE, KIND><<<grid, block, 0, s>>>(a, one_shot ? 1 : 0);
     return cudaGetLastError();
 }

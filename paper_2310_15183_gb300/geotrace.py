@@ -21,7 +21,7 @@ ERRORS = {-1: "invalid argument", -2: "not configured", -3: "CUDA error", -4: "o
           -5: "device watchdog timeout", -6: "unsupported device or feature"}
 ESCAPED, HORIZON, MAXSTEPS, NONFINITE, TIMEOUT = 0, 1, 2, 3, 4
 MODE_FP64, MODE_FP32_MIXED = 0, 1
-FLAG_COMPAT_WEIGHTS, FLAG_COMPAT_CAMERA, FLAG_ONE_SHOT, FLAG_GRAPH = 1, 2, 4, 8
+FLAG_COMPAT_WEIGHTS, FLAG_COMPAT_CAMERA, FLAG_ONE_SHOT, FLAG_GRAPH, FLAG_PRECISE_MN = 1, 2, 4, 8, 16
 
 # every symbol include/geotrace.h declares
 EXPORTS = ("gt_create", "gt_destroy", "gt_set_stream", "gt_set_spacetime", "gt_set_camera",

@@ -67,6 +67,9 @@ int main()
     g_c = Counts();
     gt::mn_rates<CN>(st, CN(5.0), CN(1.1), CN(0.2), CN(0.3), CN(0.9), CN(-2.0), o);
     const Counts mn = g_c;
+    g_c = Counts();
+    gt::mn_rates<CN, true>(st, CN(5.0), CN(1.1), CN(0.2), CN(0.3), CN(0.9), CN(-2.0), o);
+    const Counts mn_tail = g_c; // closed-form multipole tails (GT_FLAG_PRECISE_MN)
     // RK4 combination outside the four field evaluations (trace.cu, rk4_step64):
     //   h = |sp / k1.dt|: 1 div; hh = 0.5 h: 1 mul; 3 stages x 4 state fma;
     //   hw = h w: 1 mul; 6 components x (k1 + 2k2 + 2k3 + k4: 2 fma + 1 add; x + hw s: 1 fma)
@@ -81,12 +84,14 @@ int main()
     printf("{\n");
     print_counts("kerr_field", kerr, false);
     print_counts("mn_field", mn, false);
+    print_counts("mn_field_precise", mn_tail, false);
     print_counts("rk4_combination", comb, false);
     print_counts("compensated_update", comp, false);
     printf("  \"kerr_step_flops\": %ld,\n", 4 * flops(kerr) + flops(comb));
     printf("  \"mn_step_flops\": %ld,\n", 4 * flops(mn) + flops(comb));
     printf("  \"kerr_step_flops_mixed\": %ld,\n", 4 * flops(kerr) + flops(comb) + flops(comp));
-    printf("  \"mn_step_flops_mixed\": %ld\n", 4 * flops(mn) + flops(comb) + flops(comp));
+    printf("  \"mn_step_flops_mixed\": %ld,\n", 4 * flops(mn) + flops(comb) + flops(comp));
+    printf("  \"mn_step_flops_mixed_precise\": %ld\n", 4 * flops(mn_tail) + flops(comb) + flops(comp));
     printf("}\n");
     return 0;
 }

@@ -1,6 +1,8 @@
 // field_forms.cpp -- host check of the device field templates: the reverse-sweep
-// Manko-Novikov rates against the forward dual-number rates, in double and in float,
-// at seeded random phase-space points of several (alpha, k, beta) spacetimes.
+// Manko-Novikov rates (direct multipole sums, as the FP64 kernels run them, and the
+// closed-form series tails of the FP32 kernels) against the forward dual-number rates,
+// in double and in float, at seeded random phase-space points of several (alpha, k,
+// beta) spacetimes.
 // Prints the largest relative differences (against the largest rate component) of
 // reverse vs forward in double, and of float reverse vs double reverse at the points
 // where the float forward form is finite (both float forms overflow together where the
@@ -38,7 +40,7 @@ static double rel(double a, double b, double scale) { return fabs(a - b) / scale
 
 int main()
 {
-    double worst_fwd = 0.0, worst_f32 = 0.0, worst_f32_fwd = 0.0;
+    double worst_fwd = 0.0, worst_tail = 0.0, worst_f32 = 0.0, worst_f32_fwd = 0.0;
     long n = 0, n_f32 = 0, finite_mismatch = 0;
     const double Ms[] = {0.5, 1.0};
     for (double M : Ms)
@@ -66,11 +68,13 @@ int main()
             for (int i = 0; i < 400; ++i) {
                 const double r = c.r_plus + uni(0.3, 40.0) * M, th = uni(0.05, M_PI - 0.05);
                 const double pr = uni(-2, 2), pth = uni(-3, 3), pt = -1.0, pph = uni(-4, 4);
-                gt::Rates<double> o1, o2;
+                gt::Rates<double> o1, o2, o3;
                 gt::mn_rates<double>(c, r, th, pr, pth, pt, pph, o1);
                 gt::mn_rates_fwd<double>(c, r, th, pr, pth, pt, pph, o2);
+                gt::mn_rates<double, true>(c, r, th, pr, pth, pt, pph, o3); // the FP32 form
                 const double v1[6] = {o1.dt, o1.dr, o1.dth, o1.dph, o1.dpr, o1.dpth};
                 const double v2[6] = {o2.dt, o2.dr, o2.dth, o2.dph, o2.dpr, o2.dpth};
+                const double v3[6] = {o3.dt, o3.dr, o3.dth, o3.dph, o3.dpr, o3.dpth};
                 double scale = 0.0;
                 for (int j = 0; j < 6; ++j) scale = fmax(scale, fabs(v2[j]));
                 if (!(scale > 0.0) || !isfinite(scale)) continue;
@@ -84,6 +88,7 @@ int main()
                 bool fin_f = true, fin_g = true;
                 for (int j = 0; j < 6; ++j) {
                     worst_fwd = fmax(worst_fwd, rel(v1[j], v2[j], scale));
+                    worst_tail = fmax(worst_tail, rel(v3[j], v2[j], scale));
                     fin_f = fin_f && isfinite(vf[j]);
                     fin_g = fin_g && isfinite(vg[j]);
                 }
@@ -98,8 +103,9 @@ int main()
                 ++n;
             }
         }
-    printf("{\"points\": %ld, \"reverse_vs_forward_f64\": %.3e, \"points_f32\": %ld, "
+    printf("{\"points\": %ld, \"reverse_vs_forward_f64\": %.3e, \"tail_form_vs_forward_f64\": %.3e, "
+           "\"points_f32\": %ld, "
            "\"f32_vs_f64\": %.3e, \"f32_forward_vs_f64\": %.3e, \"finite_mismatch\": %ld}\n",
-           n, worst_fwd, n_f32, worst_f32, worst_f32_fwd, finite_mismatch);
+           n, worst_fwd, worst_tail, n_f32, worst_f32, worst_f32_fwd, finite_mismatch);
     return 0;
 }

@@ -268,6 +268,20 @@ def test_mixed_terminating_classification_and_angle(tracer, oracle, cam, n_steps
     assert rep["agree"] >= 0.999 and rep["max_angle_escaped"] <= 1e-3, rep
 
 
+def test_mixed_precise_mn_multipole_tails(g, tracer, oracle):
+    """GT_FLAG_PRECISE_MN (closed-form multipole tails in the FP32 field): Manko-Novikov
+    terminating rays against the oracle -- the same classification, and end angles of
+    escaped rays two orders of magnitude closer than the mixed-precision bound."""
+    cam = W.sub_camera(MN, 12, 10)
+    ref = run_oracle(oracle, cam, 500000, 1.5e-4, want_min_sin=True)
+    band = neighbour_band(ref["status"], cam.res_x, cam.res_y) | (ref["min_sin"] < 1e-3)
+    got = run_gpu(tracer, cam, 500000, 1.5e-4, mode=1, flags=g.FLAG_PRECISE_MN)
+    rep = mixed_report(got, ref, exclude=band)
+    assert rep["agree"] >= 0.999 and rep["max_angle_escaped"] <= 1e-5, rep
+    plain = run_gpu(tracer, cam, 500000, 1.5e-4, mode=1)
+    assert not np.array_equal(plain["th"], got["th"])  # the other field form ran
+
+
 def test_mixed_reprojection_interval(tracer, oracle):
     """H = 0 re-projection of p_r (FP64, every K steps): with K = 16 (re-projecting
     hundreds of times per ray) and with K beyond the step cap (never), the mixed path

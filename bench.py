@@ -516,7 +516,7 @@ def main():
         peak = FP64_NOMINAL
         peak_note = "FP64 dense 1.25 TFLOP/s (nominal)"
         measured_peak = geotrace.measure_fma_peak(local, fp64=True, iters=200)
-    kname = f"trace_kernel<{2 if mode else 0},{1 if cam.Q != 0 else 0}>"
+    kname = f"trace_kernel<{2 if mode else 0},{1 if cam.Q != 0 else 0},0>"
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": measured_traffic(kname, n), "kernel": kname,

@@ -197,12 +197,13 @@ template <class T>
 GT_HD void mkvar(V1<T> &o, T v, T, T) { o = {v}; }
 
 // ------------------------------------------------------------------ Kerr
+// The rate functions take theta through s = sin(theta) and cs = cos(theta) (the *_sc
+// forms), so that a caller that already has them -- the FP32 RK4 step rotates the first
+// stage's pair to the later stages -- need not evaluate them again.
 template <class T>
-GT_HD void kerr_rates(const SpacetimeT<T> &c, T r, T th, T pr, T pth, T pt,
-                                           T pph, Rates<T> &o)
+GT_HD void kerr_rates_sc(const SpacetimeT<T> &c, T r, T s, T cs, T pr, T pth, T pt, T pph,
+                         Rates<T> &o)
 {
-    T s, cs;
-    sincos_t(th, &s, &cs);
     const T a = T(c.a), a2 = T(c.a2), M = T(c.M);
     const T r2 = r * r, ra2 = r2 + a2;
     const T s2 = s * s;
@@ -226,6 +227,14 @@ GT_HD void kerr_rates(const SpacetimeT<T> &c, T r, T th, T pr, T pth, T pt,
     const T KiS = K * iSigma;
     o.dpr = T(-0.5) * (Kr - T(2) * r * KiS) * iSigma;
     o.dpth = T(-0.5) * fma_t(T(2) * a2 * s * cs, KiS, Kth) * iSigma;
+}
+
+template <class T>
+GT_HD void kerr_rates(const SpacetimeT<T> &c, T r, T th, T pr, T pth, T pt, T pph, Rates<T> &o)
+{
+    T s, cs;
+    sincos_t(th, &s, &cs);
+    kerr_rates_sc<T>(c, r, s, cs, pr, pth, pt, pph, o);
 }
 
 #ifdef __CUDACC__
@@ -309,12 +318,10 @@ GT_HD void mn_potentials(const SpacetimeT<T> &c, T r, T th, MNPot<N> &P)
 // arithmetic: a product costs one multiply forward and two fused multiply-adds backward
 // instead of five operations for a value and two derivatives.
 template <class T, bool TAIL = false>
-GT_HD void mn_rates(const SpacetimeT<T> &c, T r, T th, T pr, T pth, T pt, T pph,
-                    Rates<T> &o)
+GT_HD void mn_rates_sc(const SpacetimeT<T> &c, T r, T s, T cs, T pr, T pth, T pt, T pph,
+                       Rates<T> &o)
 {
     // ---- forward sweep (values)
-    T s, cs;
-    sincos_t(th, &s, &cs);
     const T ik = T(c.ik), tb = T(c.two_beta), al = T(c.alpha);
     const T x = (r - T(c.M)) * ik;
     const T xm1 = (r - T(c.r_plus)) * ik; // x - 1 without cancellation
@@ -588,6 +595,14 @@ GT_HD void mn_rates(const SpacetimeT<T> &c, T r, T th, T pr, T pth, T pt, T pph,
     const T dHth = s * (T(2) * cs * s2_b - y_b);
     o.dpr = T(-0.5) * dHr;
     o.dpth = T(-0.5) * dHth;
+}
+
+template <class T, bool TAIL = false>
+GT_HD void mn_rates(const SpacetimeT<T> &c, T r, T th, T pr, T pth, T pt, T pph, Rates<T> &o)
+{
+    T s, cs;
+    sincos_t(th, &s, &cs);
+    mn_rates_sc<T, TAIL>(c, r, s, cs, pr, pth, pt, pph, o);
 }
 
 // The same rates by forward-mode dual numbers (value, d/dr, d/dtheta) through

@@ -266,13 +266,30 @@ __device__ __forceinline__ void mixed_to64(const RayMixed &m, Ray64 &x)
 #endif
 
 template <int KIND, bool PRECISE>
-__device__ GT_FIELD_ATTR void rates_f32(const SpacetimeF &st, float r, float th, float pr,
-                                          float pth, float pt, float pph, Rates<float> &o)
+__device__ GT_FIELD_ATTR void rates_f32(const SpacetimeF &st, float r, float s, float cs,
+                                          float pr, float pth, float pt, float pph,
+                                          Rates<float> &o)
 {
     if (KIND == KIND_KERR || (KIND == 2 && st.kind == KIND_KERR))
-        kerr_rates<float>(st, r, th, pr, pth, pt, pph, o);
+        kerr_rates_sc<float>(st, r, s, cs, pr, pth, pt, pph, o);
     else
-        mn_rates<float, PRECISE>(st, r, th, pr, pth, pt, pph, o);
+        mn_rates_sc<float, PRECISE>(st, r, s, cs, pr, pth, pt, pph, o);
+}
+
+// sin and cos of theta + d from those of theta, for the small angle d a stage adds
+// (Taylor series of sin d through d^7 and cos d through d^6: truncation below 4e-10
+// for |d| <= 1/4; larger d -- not met in practice -- evaluates sincosf afresh).
+__device__ __forceinline__ void rotate_sc(float s, float c, float th, float d, float *s2, float *c2)
+{
+    if (fabsf(d) <= 0.25f) {
+        const float d2 = d * d;
+        const float sd = fmaf(d * d2, fmaf(d2, fmaf(d2, -1.0f / 5040.0f, 1.0f / 120.0f), -1.0f / 6.0f), d);
+        const float cd = fmaf(d2, fmaf(d2, fmaf(d2, -1.0f / 720.0f, 1.0f / 24.0f), -0.5f), 1.0f);
+        *s2 = fmaf(s, cd, c * sd);
+        *c2 = fmaf(c, cd, -(s * sd));
+    } else {
+        sincosf(th + d, s2, c2);
+    }
 }
 
 // One FP32 RK4 step on the compensated state; returns h (as float).
@@ -281,15 +298,21 @@ __device__ __forceinline__ float rk4_step32(const SpacetimeF &st, RayMixed &m, f
 {
     Rates<float> k1, k2, k3, k4;
     const float r = m.r.hi, th = m.th.hi, pr = m.pr.hi, pth = m.pth.hi;
-    rates_f32<KIND, PRECISE>(st, r, th, pr, pth, m.ptf, m.pphf, k1);
+    // sin/cos of theta once per step; the later stages rotate them by their small offsets
+    float s1, c1, s, c;
+    sincosf(th, &s1, &c1);
+    rates_f32<KIND, PRECISE>(st, r, s1, c1, pr, pth, m.ptf, m.pphf, k1);
     const float h = fabsf(sp / k1.dt);
     const float hh = 0.5f * h;
-    rates_f32<KIND, PRECISE>(st, fmaf(hh, k1.dr, r), fmaf(hh, k1.dth, th), fmaf(hh, k1.dpr, pr),
-                    fmaf(hh, k1.dpth, pth), m.ptf, m.pphf, k2);
-    rates_f32<KIND, PRECISE>(st, fmaf(hh, k2.dr, r), fmaf(hh, k2.dth, th), fmaf(hh, k2.dpr, pr),
-                    fmaf(hh, k2.dpth, pth), m.ptf, m.pphf, k3);
-    rates_f32<KIND, PRECISE>(st, fmaf(h, k3.dr, r), fmaf(h, k3.dth, th), fmaf(h, k3.dpr, pr),
-                    fmaf(h, k3.dpth, pth), m.ptf, m.pphf, k4);
+    rotate_sc(s1, c1, th, hh * k1.dth, &s, &c);
+    rates_f32<KIND, PRECISE>(st, fmaf(hh, k1.dr, r), s, c, fmaf(hh, k1.dpr, pr),
+                             fmaf(hh, k1.dpth, pth), m.ptf, m.pphf, k2);
+    rotate_sc(s1, c1, th, hh * k2.dth, &s, &c);
+    rates_f32<KIND, PRECISE>(st, fmaf(hh, k2.dr, r), s, c, fmaf(hh, k2.dpr, pr),
+                             fmaf(hh, k2.dpth, pth), m.ptf, m.pphf, k3);
+    rotate_sc(s1, c1, th, h * k3.dth, &s, &c);
+    rates_f32<KIND, PRECISE>(st, fmaf(h, k3.dr, r), s, c, fmaf(h, k3.dpr, pr),
+                             fmaf(h, k3.dpth, pth), m.ptf, m.pphf, k4);
     const float hw = h * w6;
     f2_add(m.t, hw * (k1.dt + 2.0f * k2.dt + 2.0f * k3.dt + k4.dt));
     f2_add(m.r, hw * (k1.dr + 2.0f * k2.dr + 2.0f * k3.dr + k4.dr));

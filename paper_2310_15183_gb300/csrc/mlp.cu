@@ -376,8 +376,8 @@ cudaError_t launch_pipe(const GemmArgs &g, int splits, cudaStream_t s)
 
 // ---------------------------------------------------------------------------------
 // Persistent warp-specialised variant (K-contiguous operands with TMA tensor maps).
-// 320 threads: warp 0 lane 0 loads A and B chunks with 2-D TMA boxes of 8 elements x
-// (128 | BN) rows -- exactly one K-column of core matrices each -- into S stages;
+// 320 threads: warp 0 lane 0 loads A and B chunks with one 2-D TMA box of 64 elements x
+// (128 | BN) rows each, 128-byte swizzled (the K-major SW128 operand layout), into S stages;
 // warp 1 lane 0 issues the MMAs into one of two TMEM accumulators; warps 2-9 drain the
 // other accumulator (bias, SiLU, stores) meanwhile, two warps per TMEM lane quarter
 // taking alternate 32-column chunks.  Stage and accumulator hand-offs are
@@ -469,11 +469,9 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
                     }
                     tc::mbar_expect_tx(FULL(s), L::STAGE);
                     const uint32_t a_dst = sbase + s * L::STAGE, b_dst = a_dst + L::A_BYTES;
-#pragma unroll
-                    for (int kb = 0; kb < BK / 8; kb++) {
-                        tc::tma_load_2d(a_dst + kb * L::A_LBO, &tmA, c * BK + kb * 8, mt * BM, FULL(s));
-                        tc::tma_load_2d(b_dst + kb * L::B_LBO, &tmB, c * BK + kb * 8, nt * BN, FULL(s));
-                    }
+                    // one 64 x rows box per operand, 128-byte swizzled by the copy engine
+                    tc::tma_load_2d(a_dst, &tmA, c * BK, mt * BM, FULL(s));
+                    tc::tma_load_2d(b_dst, &tmB, c * BK, nt * BN, FULL(s));
                 }
             }
             // copies still in flight (only after a failed wait) land before the CTA exits
@@ -502,8 +500,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
                     const uint32_t a_base = sbase + s * L::STAGE, b_base = a_base + L::A_BYTES;
 #pragma unroll
                     for (int kk = 0; kk < BK / 16; ++kk) {
-                        const uint64_t ad = tc::smem_desc(a_base + kk * 2 * L::A_LBO, L::A_LBO, 128);
-                        const uint64_t bd = tc::smem_desc(b_base + kk * 2 * L::B_LBO, L::B_LBO, 128);
+                        const uint64_t ad = tc::smem_desc_sw128(a_base + kk * 32);
+                        const uint64_t bd = tc::smem_desc_sw128(b_base + kk * 32);
                         tc::mma_f16(d, ad, bd, idesc, (c > c0 || kk > 0) ? 1u : 0u);
                     }
                     tc::mma_commit(EMPTY(s));
@@ -709,8 +707,9 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-// bf16 matrix of `rows` x `cols` (row stride `ld` elements, K = cols contiguous), boxes of
-// 8 columns x box_rows rows, zero fill outside.
+// 16-bit matrix of `rows` x `cols` (row stride `ld` elements, K = cols contiguous), boxes
+// of BK = 64 columns (128 bytes) x box_rows rows written 128-byte swizzled, zero fill
+// outside.
 bool make_map(CUtensorMap *m, const void *base, uint64_t rows, uint64_t cols, uint64_t ld,
               uint32_t box_rows)
 {
@@ -718,10 +717,10 @@ bool make_map(CUtensorMap *m, const void *base, uint64_t rows, uint64_t cols, ui
     if (!enc || rows == 0 || cols == 0 || rows > (1ull << 32) || cols > (1ull << 32)) return false;
     cuuint64_t dims[2] = {cols, rows};
     cuuint64_t strides[1] = {ld * 2};
-    cuuint32_t box[2] = {8, box_rows};
+    cuuint32_t box[2] = {BK, box_rows};
     cuuint32_t estr[2] = {1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box,
-               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

@@ -29,6 +29,17 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
+// Descriptor of a K-major operand tile in the 128-byte swizzled layout: rows of 128 bytes
+// (64 16-bit elements of K), the 16-byte chunk j of row r stored at chunk j ^ (r % 8), in
+// 1024-byte atoms of 8 rows (stride byte offset 1024; the leading byte offset is unused
+// for this layout and set to 16).  Swizzling mode 2 in bits 61-63.  K-slices of 16
+// elements within the atom start 32 bytes apart; the atoms must be 1024-byte aligned.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr)
+{
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | (1ull << 16) | ((uint64_t)(1024u >> 4) << 32) |
+           (1ull << 46) | (2ull << 61);
+}
+
 // 32-bit instruction descriptor of kind::f16: D = F32 (bits 4-5 = 1), A and B both BF16
 // (bits 7-9 = 1, 10-12 = 1) or both FP16 (0), both K-major (bits 15, 16 = 0), N >> 3 at
 // 17, M >> 4 at 24.

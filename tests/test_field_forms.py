@@ -27,3 +27,38 @@ def test_reverse_sweep_matches_dual_numbers(tmp_path):
     assert res["tail_form_vs_forward_f64"] < 1e-10, res
     assert res["finite_mismatch"] == 0, res
     assert res["f32_vs_f64"] < 2e-3 and res["f32_vs_f64"] <= 1.5 * res["f32_forward_vs_f64"], res
+
+
+def test_multipole_tail_closed_form_against_the_series():
+    """The closed forms the FP32 kernels use with GT_FLAG_PRECISE_MN for the Manko-Novikov
+    sums, Sa - 1 = -t^3 N(t)/(1 + s Q(t)) and Sb + 1 = -t^3 N(-t)/(1 + s' Q(-t)), against the
+    Legendre series they stand for, summed term by term to convergence (t = 1/R,
+    u = x y / R, R^2 = x^2 + y^2 - 1; the full sums are 1/(x - y) and 1/(x + y))."""
+    import numpy as np
+    rng = np.random.Generator(np.random.PCG64(2310))
+    for _ in range(200):
+        x = 1.0 + rng.uniform(0.5, 30.0)
+        y = rng.uniform(-0.999, 0.999)
+        R = np.sqrt(x * x + y * y - 1.0)
+        t, u = 1.0 / R, x * y / R
+        P = [1.0, u]
+        for l in range(1, 400):
+            P.append(((2 * l + 1) * u * P[l] - l * P[l - 1]) / (l + 1))
+        terms = np.array([P[l] * t ** (l + 1) for l in range(401)])
+        alt = terms * (-1.0) ** np.arange(401)
+        # the series do sum to 1/(x - y) and 1/(x + y)
+        assert abs(terms.sum() - 1.0 / (x - y)) < 1e-12 * (1.0 / (x - y))
+        assert abs(alt.sum() - 1.0 / (x + y)) < 1e-12 * (1.0 / (x + y))
+        Ea_series = -(x - y) * terms[3:].sum()  # Sa - 1
+        Eb_series = (x + y) * alt[3:].sum()     # Sb + 1 (Sb = -(x + y) sum_{l<=2} (-1)^l ...)
+        P2, P3 = P[2], P[3]
+        c4 = P2 * P2 - 4 * u * u * P2 + 2 * P2 + u * u
+        c5 = 2 * u * P2 * (1 - P2)
+        c6 = P2 * P2
+        N = lambda tt: 2 * P3 - c4 * tt - c5 * tt ** 2 - c6 * tt ** 3
+        Q = lambda tt: 1 + u * tt + P2 * tt ** 2
+        Ea = -t ** 3 * N(t) / (1 + (x - y) * t * Q(t))
+        Eb = -t ** 3 * N(-t) / (1 + (x + y) * t * Q(-t))
+        scale = t ** 4 * (x + 1)
+        assert abs(Ea - Ea_series) < 1e-10 * scale, (x, y, Ea, Ea_series)
+        assert abs(Eb - Eb_series) < 1e-10 * scale, (x, y, Eb, Eb_series)

@@ -32,7 +32,6 @@ from paper_2310_15183_gb300 import workloads as W  # noqa: E402
 
 METRIC = "RK4 geodesic steps/s & rays/s on GB300: FP64 plain vs FP32-mixed vs surrogate"
 UNIT = "RK4 steps/s"
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 MAX_SM_MHZ = 2070.0
 FP64_NOMINAL = 1.25e12  # GB300 dense FP64 (non-tensor) FLOP/s
@@ -509,8 +508,9 @@ def main():
     kernel_s = t_dev / args.steps
     achieved = flops_per_step * steps_per_pass / kernel_s
     if mode == geotrace.MODE_FP32_MIXED:
-        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6
-        peak_note = "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)"
+        sms = tr.sm_count()
+        peak = sms * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6
+        peak_note = f"FP32 FMA: {sms} SMs x 128 lanes x 2 flop x 2070 MHz (derived)"
         measured_peak = geotrace.measure_fma_peak(local, fp64=False)
     else:
         peak = FP64_NOMINAL

@@ -264,11 +264,13 @@ int gt_surrogate_infer(gt_ctx *ctx, gt_surrogate *s, float tau, double band, flo
  * the process exits.  The caller still owns and passes the device output arrays
  * (layout as gt_trace_batch; default launch options, no watchdog).  In FP32-mixed
  * mode the FP64 zone steps run inline in the FP32 kernel (H = 0 re-projection every
- * 64 steps), because the park lists gt_trace_batch uses would need allocated memory;
- * FP64 results are identical to gt_trace_batch's.  The first call on a device looks up that array's
- * device address (cudaGetSymbolAddress, with the device current); make that first
- * call before any stream capture.  The call uploads the descriptors, synchronises
- * `cuda_stream` to check them, clears the queue counter and launches asynchronously.
+ * 4096 steps, the context's default), because the park lists gt_trace_batch uses would
+ * need allocated memory; FP64 results are identical to gt_trace_batch's.  Each call
+ * looks up that array's device address on `device` once per process (with the device
+ * current) and keeps it, so the entry point must not be used on a device across a
+ * cudaDeviceReset of that device.  The call uploads the descriptors and synchronises
+ * `cuda_stream` to check them, so it cannot be issued while that stream is being
+ * captured; it then clears the queue counter and launches asynchronously.
  * All calls share the array and it keeps the last call's contents: calls whose work
  * overlaps on the GPU (other streams, other host threads) race and must not be issued.
  * Errors: GT_ERR_INVALID_ARG (including n_cams > GT_NOALLOC_MAX_CAMS, or a camera

@@ -69,6 +69,8 @@ def _load():
         lib.or_hamiltonian.restype = i
         lib.or_camera_ray.argtypes = [d, d, d, d, d, d, i, i, i, i, i, pd, pd]
         lib.or_camera_ray.restype = i
+        lib.or_camera_dir.argtypes = [d, d, d, d, d, d, d, i, pd, pd]
+        lib.or_camera_dir.restype = i
         lib.or_trace_ray.argtypes = [d, d, d, pd, pd, d, i64, d, i, pi, pi64, pd]
         lib.or_trace_ray.restype = i
         lib.or_trace_ray_path.argtypes = [d, d, d, pd, pd, d, i64, d, i, pd, i64, pi64]
@@ -151,6 +153,14 @@ def camera_ray(M, S, Q, r0, th0, fov_deg, resX, resY, i, j, flags=0):
     q, p = _arr(4), _arr(4)
     _check(_load().or_camera_ray(M, S, Q, r0, th0, fov_deg, resX, resY, i, j, flags, q, p),
            "camera_ray")
+    return np.array(q[:]), np.array(p[:])
+
+
+def camera_dir(M, S, Q, r0, th0, alpha, beta, flags=0):
+    """Initial (q, p) of the ray leaving a camera at (r0, th0) in direction (alpha, beta)."""
+    q, p = _arr(4), _arr(4)
+    _check(_load().or_camera_dir(M, S, Q, r0, th0, float(alpha), float(beta), flags, q, p),
+           "camera_dir")
     return np.array(q[:]), np.array(p[:])
 
 

@@ -394,19 +394,14 @@ static double hamiltonian(const spacetime *st, const double q[4], const double p
 /* Camera (appendix listing + Sec. 3.3.1)                                     */
 /* ------------------------------------------------------------------------ */
 
-/* Pixel (i, j), i in [0, resX) along phi, j in [0, resY) along theta.
- * V = tan(FOV/2)/r0, H = atan(tan(V) resX/resY); alpha_i, beta_j are the
- * inclusive linspaces over [-H, H] and [-V, V] (a single pixel sits at 0).
- * v = (T, -1, beta_j, alpha_i / sin(theta0)), T the root
- * (-B + sqrt(B^2 - 4AC))/(2A) of g_{mu nu} v^mu v^nu = 0, then v /= |T| so
- * that v^t = -1 (Sec. 3.3.1), and p_mu = g_{mu nu} v^nu at q0 = (0, r0, theta0, 0). */
-static int camera_ray(const spacetime *st, double r0, double th0, double fov_deg, int resX,
-                      int resY, int i, int j, int flags, double q[4], double p[4])
+/* Initial data of one ray leaving the camera at (0, r0, th0, 0) in the direction
+ * (alpha, beta) of the camera's (v^phi sin th0, v^theta) plane (Sec. 3.3.1 and the
+ * listing's camera block): v = (v^t, -1, beta, alpha/sin th0), v^t the root
+ * (-B + sqrt(B^2 - 4AC))/(2A) of g(v, v) = 0, v rescaled so that v^t = -1 (READING),
+ * p_mu = g_{mu nu} v^nu. */
+static int camera_dir(const spacetime *st, double r0, double th0, double al, double bt, int flags,
+                      double q[4], double p[4])
 {
-    const double V = tan(0.5 * fov_deg / 180.0 * M_PI) / r0;
-    const double Hh = atan(tan(V) * (double)resX / (double)resY);
-    const double al = resX > 1 ? Hh * (double)(2 * i - (resX - 1)) / (double)(resX - 1) : 0.0;
-    const double bt = resY > 1 ? V * (double)(2 * j - (resY - 1)) / (double)(resY - 1) : 0.0;
     double v[4];
     v[1] = -1.0;
     v[2] = bt;
@@ -434,6 +429,20 @@ static int camera_ray(const spacetime *st, double r0, double th0, double fov_deg
         p[m] = acc;
     }
     return OR_OK;
+}
+
+/* Pixel (i, j) of a resX x resY camera, i in [0, resX) along phi, j in [0, resY)
+ * along theta: alpha_i, beta_j the inclusive linspaces over [-H, H] and [-V, V],
+ * V = tan(FOV/2)/r0, H = atan(tan(V) resX/resY) (listing's camera block); a single
+ * pixel sits at 0 (READING). */
+static int camera_ray(const spacetime *st, double r0, double th0, double fov_deg, int resX,
+                      int resY, int i, int j, int flags, double q[4], double p[4])
+{
+    const double V = tan(0.5 * fov_deg / 180.0 * M_PI) / r0;
+    const double Hh = atan(tan(V) * (double)resX / (double)resY);
+    const double al = resX > 1 ? Hh * (double)(2 * i - (resX - 1)) / (double)(resX - 1) : 0.0;
+    const double bt = resY > 1 ? V * (double)(2 * j - (resY - 1)) / (double)(resY - 1) : 0.0;
+    return camera_dir(st, r0, th0, al, bt, flags, q, p);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -655,6 +664,17 @@ int or_camera_ray(double M, double S, double Q, double r0, double th0, double fo
     if (!camera_valid(r0, th0, fov_deg, resX, resY)) return OR_ERR_INVALID_ARG;
     if (i < 0 || i >= resX || j < 0 || j >= resY) return OR_ERR_INVALID_ARG;
     return camera_ray(&st, r0, th0, fov_deg, resX, resY, i, j, flags, q4, p4);
+}
+
+/* Initial (q, p) of a ray in direction (alpha, beta) from a camera at (r0, th0). */
+int or_camera_dir(double M, double S, double Q, double r0, double th0, double al, double bt,
+                  int flags, double *q4, double *p4)
+{
+    spacetime st;
+    if (spacetime_init(&st, M, S, Q) != OR_OK) return OR_ERR_INVALID_ARG;
+    if (!(r0 > 0.0) || !isfinite(r0) || !(th0 > 0.0 && th0 < M_PI)) return OR_ERR_INVALID_ARG;
+    if (!isfinite(al) || !isfinite(bt)) return OR_ERR_INVALID_ARG;
+    return camera_dir(&st, r0, th0, al, bt, flags, q4, p4);
 }
 
 /* Integrate one ray from an arbitrary initial state (q, p are overwritten by

@@ -13,6 +13,9 @@
 #include "internal.cuh"
 
 using gt::CamDesc;
+using gt::fill_desc;
+using gt::valid_camera;
+using gt::valid_spacetime;
 
 struct gt_ctx {
     int device = 0;
@@ -83,38 +86,6 @@ int cuda_code(cudaError_t e)
     if (e == cudaSuccess) return GT_OK;
     if (e == cudaErrorMemoryAllocation) return GT_ERR_OOM;
     return GT_ERR_CUDA;
-}
-
-bool valid_spacetime(double M, double S, double Q)
-{
-    if (!(M > 0.0) || !isfinite(M) || !isfinite(S) || !isfinite(Q)) return false;
-    if (!(fabs(S) < M * M)) return false;
-    if (Q != 0.0 && S == 0.0) return false;
-    return true;
-}
-
-bool valid_camera(double r0, double th0, double fov, int rx, int ry)
-{
-    if (!(r0 > 0.0) || !isfinite(r0)) return false;
-    if (!(th0 > 0.0 && th0 < M_PI)) return false;
-    if (!(fov > 0.0 && fov < 180.0)) return false;
-    if (rx < 1 || ry < 1) return false;
-    return true;
-}
-
-void fill_desc(CamDesc &d, double M, double S, double Q, double r0, double th0, double fov,
-               int rx, int ry, int64_t offset)
-{
-    memset(&d, 0, sizeof d);
-    d.M = M;
-    d.S = S;
-    d.Q = Q;
-    d.r0 = r0;
-    d.th0 = th0;
-    d.fov_deg = fov;
-    d.res_x = rx;
-    d.res_y = ry;
-    d.offset = offset;
 }
 
 gt_options effective(const gt_options &o)

@@ -2,7 +2,9 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "../../include/geotrace.h"
 #include "spacetime.cuh"
@@ -89,6 +91,42 @@ struct TraceArgs {
     uint32_t *nsteps;
     unsigned long long *scratch; // SCR_WORDS words
 };
+
+// Host-side validation shared by every entry point that takes a spacetime or a camera
+// (Sec. 2.2.2: |S| < M^2 for a black hole; Sec. 2.2.3: alpha divides by S/M, so q != 0
+// needs S != 0; Sec. 3.3.1: a pinhole camera at 0 < theta0 < pi with 0 < FOV < 180 deg).
+inline bool valid_spacetime(double M, double S, double Q)
+{
+    if (!(M > 0.0) || !isfinite(M) || !isfinite(S) || !isfinite(Q)) return false;
+    if (!(fabs(S) < M * M)) return false;
+    if (Q != 0.0 && S == 0.0) return false;
+    return true;
+}
+
+inline bool valid_camera(double r0, double th0, double fov, int rx, int ry)
+{
+    if (!(r0 > 0.0) || !isfinite(r0)) return false;
+    if (!(th0 > 0.0 && th0 < M_PI)) return false;
+    if (!(fov > 0.0 && fov < 180.0)) return false;
+    if (rx < 1 || ry < 1) return false;
+    return true;
+}
+
+// Raw descriptor of one camera (the derived fields are filled in on the device).
+inline void fill_desc(CamDesc &d, double M, double S, double Q, double r0, double th0, double fov,
+                      int rx, int ry, int64_t offset)
+{
+    memset(&d, 0, sizeof d);
+    d.M = M;
+    d.S = S;
+    d.Q = Q;
+    d.r0 = r0;
+    d.th0 = th0;
+    d.fov_deg = fov;
+    d.res_x = rx;
+    d.res_y = ry;
+    d.offset = offset;
+}
 
 // Launchers (trace.cu).  Return a cudaError_t from the launch.
 cudaError_t launch_camera_setup(CamDesc *d_cams, int n_cams, int flags, double r_switch,

@@ -30,7 +30,9 @@ std::mutex g_lock;
 void *g_addr[MAX_DEVICES] = {};
 
 // Device address of the array on `device` (which must be current); looked up once per
-// device.  In host code the symbol is only a stand-in, never a device address.
+// device and kept for the life of the process, so the entry point must not be used on a
+// device across a cudaDeviceReset of it (the module, and the array with it, is reloaded).
+// In host code the symbol is only a stand-in, never a device address.
 int scratch_address(int device, unsigned char **out)
 {
     if (device < 0 || device >= MAX_DEVICES) return GT_ERR_UNSUPPORTED;
@@ -43,18 +45,6 @@ int scratch_address(int device, unsigned char **out)
     }
     *out = (unsigned char *)g_addr[device];
     return GT_OK;
-}
-
-bool ok_spacetime(double M, double S, double Q)
-{
-    return M > 0.0 && isfinite(M) && isfinite(S) && isfinite(Q) && fabs(S) < M * M &&
-           !(Q != 0.0 && S == 0.0);
-}
-
-bool ok_camera(double r0, double th0, double fov, int rx, int ry)
-{
-    return r0 > 0.0 && isfinite(r0) && th0 > 0.0 && th0 < M_PI && fov > 0.0 && fov < 180.0 &&
-           rx >= 1 && ry >= 1;
 }
 
 struct DeviceRestore {
@@ -85,18 +75,10 @@ extern "C" int gt_trace_batch_noalloc(int device, void *cuda_stream, const gt_ca
     bool any_mn = false, any_kerr = false;
     for (int i = 0; i < n_cams; i++) {
         const gt_camera_desc &d = cams[i];
-        if (!ok_spacetime(d.M, d.S, d.Q) || !ok_camera(d.r0, d.theta0, d.fov_deg, d.res_x, d.res_y))
+        if (!gt::valid_spacetime(d.M, d.S, d.Q) ||
+            !gt::valid_camera(d.r0, d.theta0, d.fov_deg, d.res_x, d.res_y))
             return GT_ERR_INVALID_ARG;
-        memset(&h[i], 0, sizeof h[i]);
-        h[i].M = d.M;
-        h[i].S = d.S;
-        h[i].Q = d.Q;
-        h[i].r0 = d.r0;
-        h[i].th0 = d.theta0;
-        h[i].fov_deg = d.fov_deg;
-        h[i].res_x = d.res_x;
-        h[i].res_y = d.res_y;
-        h[i].offset = total;
+        gt::fill_desc(h[i], d.M, d.S, d.Q, d.r0, d.theta0, d.fov_deg, d.res_x, d.res_y, total);
         total += (int64_t)d.res_x * d.res_y;
         if (d.Q != 0.0)
             any_mn = true;
@@ -150,7 +132,7 @@ extern "C" int gt_trace_batch_noalloc(int device, void *cuda_stream, const gt_ca
     a.sp = step_precision;
     a.w6 = 1.0 / 6.0;
     a.flags = 0;
-    a.reproject_every = 64;
+    a.reproject_every = 4096; // the context's default interval
     a.timeout_ns = 0;
     a.t = t;
     a.r = r;

@@ -3,11 +3,14 @@
 // BF16 or FP16 operands and FP32 accumulation in TMEM, commit to an mbarrier, TMEM
 // loads, and the TMA bulk-tensor loads, stores and reductions with their mbarriers.
 //
-// Operand layout in shared memory: K-major, no swizzle, 8x8 "core matrices" of
-// 8 rows x 16 bytes.  Core matrix (g, kb) -- row group g = row/8, column block
-// kb = k/8 -- sits at  kb * lbo + g * 128  bytes, so the descriptor's leading byte
-// offset (between core matrices along K) is `lbo` and the stride byte offset
-// (between 8-row groups) is 128.
+// Two operand layouts in shared memory, both K-major:
+//   - the 128-byte swizzled layout of the warp-specialised TMA kernel (smem_desc_sw128),
+//     written by one TMA box per operand per 64-wide K-chunk; and
+//   - the no-swizzle core-matrix layout of the cp.async / register-staged fallback
+//     kernels (smem_desc): 8x8 "core matrices" of 8 rows x 16 bytes, core matrix
+//     (g, kb) -- row group g = row/8, column block kb = k/8 -- at kb * lbo + g * 128
+//     bytes, so the leading byte offset (between core matrices along K) is `lbo` and
+//     the stride byte offset (between 8-row groups) is 128.
 #pragma once
 
 #include <cuda_runtime.h>

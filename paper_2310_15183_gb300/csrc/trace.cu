@@ -23,6 +23,7 @@
 
 #include "../../include/geotrace.h"
 #include "camera.cuh"
+#include "compensated.cuh"
 #include "internal.cuh"
 #include "spacetime.cuh"
 
@@ -121,34 +122,38 @@ cudaError_t launch_camera_setup(CamDesc *d_cams, int n_cams, int flags, double r
 }
 
 template <int KIND>
-__device__ __forceinline__ void rates_any(const SpacetimeC &st, double r, double th, double pr,
-                                          double pth, double pt, double pph, Rates<double> &o)
+__device__ __forceinline__ void rates_any(const SpacetimeC &st, double r, double s, double cs,
+                                          double pr, double pth, double pt, double pph,
+                                          Rates<double> &o)
 {
-    if (KIND == 2) {
-        if (st.kind == KIND_KERR)
-            kerr_rates<double>(st, r, th, pr, pth, pt, pph, o);
-        else
-            mn_rates<double>(st, r, th, pr, pth, pt, pph, o);
-    } else {
-        rates<KIND, double>(st, r, th, pr, pth, pt, pph, o);
-    }
+    if (KIND == KIND_KERR || (KIND == 2 && st.kind == KIND_KERR))
+        kerr_rates_sc<double>(st, r, s, cs, pr, pth, pt, pph, o);
+    else
+        mn_rates_sc<double>(st, r, s, cs, pr, pth, pt, pph, o);
 }
 
-// One FP64 RK4 step; returns h and writes the candidate state to y.
+// One FP64 RK4 step; returns h and writes the candidate state to y.  sin and cos of
+// theta are evaluated once per step and rotated to the later stages by their small
+// angle offsets (Taylor series, FP64 accurate).
 template <int KIND>
 __device__ __forceinline__ double rk4_step64(const SpacetimeC &st, const Ray64 &x, double sp,
                                              double w6, Ray64 &y)
 {
     Rates<double> k1, k2, k3, k4;
-    rates_any<KIND>(st, x.r, x.th, x.pr, x.pth, x.pt, x.pph, k1);
+    double s1, c1, s, c;
+    sincos(x.th, &s1, &c1);
+    rates_any<KIND>(st, x.r, s1, c1, x.pr, x.pth, x.pt, x.pph, k1);
     const double h = fabs(sp / k1.dt);
     const double hh = 0.5 * h;
-    rates_any<KIND>(st, x.r + hh * k1.dr, x.th + hh * k1.dth, x.pr + hh * k1.dpr,
-                    x.pth + hh * k1.dpth, x.pt, x.pph, k2);
-    rates_any<KIND>(st, x.r + hh * k2.dr, x.th + hh * k2.dth, x.pr + hh * k2.dpr,
-                    x.pth + hh * k2.dpth, x.pt, x.pph, k3);
-    rates_any<KIND>(st, x.r + h * k3.dr, x.th + h * k3.dth, x.pr + h * k3.dpr,
-                    x.pth + h * k3.dpth, x.pt, x.pph, k4);
+    rotate_sc(s1, c1, x.th, hh * k1.dth, &s, &c);
+    rates_any<KIND>(st, x.r + hh * k1.dr, s, c, x.pr + hh * k1.dpr, x.pth + hh * k1.dpth, x.pt,
+                    x.pph, k2);
+    rotate_sc(s1, c1, x.th, hh * k2.dth, &s, &c);
+    rates_any<KIND>(st, x.r + hh * k2.dr, s, c, x.pr + hh * k2.dpr, x.pth + hh * k2.dpth, x.pt,
+                    x.pph, k3);
+    rotate_sc(s1, c1, x.th, h * k3.dth, &s, &c);
+    rates_any<KIND>(st, x.r + h * k3.dr, s, c, x.pr + h * k3.dpr, x.pth + h * k3.dpth, x.pt,
+                    x.pph, k4);
     const double hw = h * w6;
     y.t = x.t + hw * (k1.dt + 2.0 * k2.dt + 2.0 * k3.dt + k4.dt);
     y.r = x.r + hw * (k1.dr + 2.0 * k2.dr + 2.0 * k3.dr + k4.dr);
@@ -203,28 +208,6 @@ __device__ __forceinline__ int exit_status(double r, double h, double r_esc, dou
 }
 
 // ------------------------------------------------------------------ FP32-mixed pieces
-// Compensated (hi, lo) float pair: x = hi + lo with |lo| <= ulp(hi)/2.
-struct F2 {
-    float hi, lo;
-};
-__device__ __forceinline__ F2 f2_from(double v)
-{
-    const float h = (float)v;
-    return {h, (float)(v - (double)h)};
-}
-__device__ __forceinline__ double f2_to(F2 a) { return (double)a.hi + (double)a.lo; }
-// a += d with an error-free TwoSum, then renormalise.
-__device__ __forceinline__ void f2_add(F2 &a, float d)
-{
-    const float s = a.hi + d;
-    const float bb = s - a.hi;
-    const float e = (a.hi - (s - bb)) + (d - bb);
-    const float lo = a.lo + e;
-    const float s2 = s + lo;
-    a.lo = lo - (s2 - s);
-    a.hi = s2;
-}
-
 struct RayMixed {
     F2 t, r, th, ph, pr, pth;
     double pt, pph; // constants of motion kept in FP64
@@ -274,22 +257,6 @@ __device__ GT_FIELD_ATTR void rates_f32(const SpacetimeF &st, float r, float s, 
         kerr_rates_sc<float>(st, r, s, cs, pr, pth, pt, pph, o);
     else
         mn_rates_sc<float, PRECISE>(st, r, s, cs, pr, pth, pt, pph, o);
-}
-
-// sin and cos of theta + d from those of theta, for the small angle d a stage adds
-// (Taylor series of sin d through d^7 and cos d through d^6: truncation below 4e-10
-// for |d| <= 1/4; larger d -- not met in practice -- evaluates sincosf afresh).
-__device__ __forceinline__ void rotate_sc(float s, float c, float th, float d, float *s2, float *c2)
-{
-    if (fabsf(d) <= 0.25f) {
-        const float d2 = d * d;
-        const float sd = fmaf(d * d2, fmaf(d2, fmaf(d2, -1.0f / 5040.0f, 1.0f / 120.0f), -1.0f / 6.0f), d);
-        const float cd = fmaf(d2, fmaf(d2, fmaf(d2, -1.0f / 720.0f, 1.0f / 24.0f), -0.5f), 1.0f);
-        *s2 = fmaf(s, cd, c * sd);
-        *c2 = fmaf(c, cd, -(s * sd));
-    } else {
-        sincosf(th + d, s2, c2);
-    }
 }
 
 // One FP32 RK4 step on the compensated state; returns h (as float).

@@ -78,9 +78,10 @@ int main()
     comb.mul = 2;
     comb.fma = 12 + 6 * 3;
     comb.add = 6;
-    // FP32-mixed adds a compensated TwoSum + renormalisation (10 adds) per component
+    // FP32-mixed adds the compensated update (increment into the low part, then Fast2Sum:
+    // 4 adds) per component (compensated.cuh, f2_add)
     Counts comp;
-    comp.add = 6 * 10;
+    comp.add = 6 * 4;
     printf("{\n");
     print_counts("kerr_field", kerr, false);
     print_counts("mn_field", mn, false);

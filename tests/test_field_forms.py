@@ -62,3 +62,17 @@ def test_multipole_tail_closed_form_against_the_series():
         scale = t ** 4 * (x + 1)
         assert abs(Ea - Ea_series) < 1e-10 * scale, (x, y, Ea, Ea_series)
         assert abs(Eb - Eb_series) < 1e-10 * scale, (x, y, Eb, Eb_series)
+
+
+def test_compensated_update_error_bound(tmp_path):
+    """The FP32-mixed state update (low part first, then Fast2Sum) stays within
+    sum_k (u |d_k| + u^2 |hi_k|) of the exact sum -- including a momentum driven through
+    zero, where hi is the smaller term -- and keeps |lo| <= ulp(hi)/2 (<= ulp(hi) at a zero
+    crossing, where Fast2Sum's precondition can fail for a step)."""
+    exe = str(tmp_path / "compensated_sum")
+    subprocess.run(["g++", "-std=c++17", "-O1", "-ffp-contract=off",
+                    os.path.join(HERE, "compensated_sum.cpp"), "-o", exe], check=True)
+    res = json.loads(subprocess.run([exe], check=True, capture_output=True, text=True).stdout)
+    for name, (ratio, lo) in res.items():
+        assert ratio <= 1.0, (name, res)
+        assert lo <= (1.0 if name == "zero_crossing" else 0.5), (name, res)

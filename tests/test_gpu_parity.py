@@ -376,3 +376,77 @@ def test_pixel_list_trace_matches_full_image(tracer):
         torch.cuda.synchronize()
         for k in ("t", "r", "th", "ph", "status", "nsteps"):
             assert np.array_equal(sub[k], full[k][pix]), (mode, k)
+
+
+# ----------------------------------------------------------------- per-ray initial data
+def kerr_rmin(M, a, r0, p, th0, n_grid=4000):
+    """min over r in (r_+, r0] of R(r)/(E^2 r^4), R the Kerr radial potential of the ray's
+    constants of motion E = -p_t, L = p_phi and Carter constant K (dense geometric grid)."""
+    E, L = -p[0], p[3]
+    K = p[2] ** 2 + np.cos(th0) ** 2 * (-a * a * E * E + L * L / np.sin(th0) ** 2)
+    rp = M + np.sqrt(M * M - a * a)
+    r = np.exp(np.linspace(np.log(rp * 1.0001), np.log(r0), n_grid))
+    R = (E * (r * r + a * a) - a * L) ** 2 - (r * r - 2 * M * r + a * a) * ((L - a * E) ** 2 + K)
+    return float(np.min(R / (E * E * r ** 4)))
+
+
+def _oracle_rays(oracle, M, r0, al, be, spin, q, th0, n_steps, sp):
+    from concurrent.futures import ThreadPoolExecutor
+
+    def one(k):
+        S = spin[k] * M * M
+        q0, p0 = oracle.camera_dir(M, S, q[k], r0, th0[k], al[k], be[k])
+        qe, pe, st, ns, ms = oracle.trace_ray(M, S, q[k], q0, p0, r0, n_steps, sp)
+        return qe, st, ns, ms, p0
+    with ThreadPoolExecutor(max_workers=16) as ex:
+        res = list(ex.map(one, range(len(al))))
+    out = {k: np.array([x[0][i] for x in res]) for i, k in enumerate(("t", "r", "th", "ph"))}
+    out["status"] = np.array([x[1] for x in res], np.uint8)
+    out["nsteps"] = np.array([x[2] for x in res], np.uint32)
+    out["min_sin"] = np.array([x[3] for x in res])
+    out["p0"] = np.array([x[4] for x in res])
+    return out
+
+
+def test_per_ray_trace_matches_oracle(tracer, oracle):
+    """gt_trace_rays (the surrogate's label generator: spacetime and camera per ray) against
+    the oracle's per-ray camera and integrator, FP64: 200 rays over the training ranges
+    (a/M in [0, 0.99], inclination 5-90 deg, 40 of them Manko-Novikov with q in [-2, 2]),
+    element-wise 1e-9 with equal status and step count at a 3,000-step cap; then the Kerr
+    rays to termination, outside the photon-ring band and axis crossings."""
+    M, r0, sp = 0.5, 15.0, 1.5e-4
+    al, be, spin, q, th0 = W.surrogate_samples(200, seed=77, M=M, r0=r0)
+    rng = np.random.Generator(np.random.PCG64(78))
+    spin[:40] = rng.uniform(0.1, 0.99, 40)  # Manko-Novikov needs S != 0
+    q[:40] = rng.uniform(-2.0, 2.0, 40)
+    dev = [torch.tensor(x, dtype=torch.float64, device="cuda") for x in (al, be, spin, q, th0)]
+    got = to_numpy(tracer.trace_rays(*dev, M, r0, 3000, sp, 0))
+    torch.cuda.synchronize()
+    ref = _oracle_rays(oracle, M, r0, al, be, spin, q, th0, 3000, sp)
+    assert_fp64_parity(got, ref, what="per-ray 3000")
+    kerr = slice(40, 200)
+    args = [x[kerr] for x in (al, be, spin, q, th0)]
+    got = to_numpy(tracer.trace_rays(*[d[kerr] for d in dev], M, r0, 400000, sp, 0))
+    torch.cuda.synchronize()
+    ref = _oracle_rays(oracle, M, r0, *args, 400000, sp)
+    band = np.array([abs(kerr_rmin(M, a * M, r0, p, t)) < 1e-3
+                     for a, p, t in zip(args[2], ref["p0"], args[4])]) | (ref["min_sin"] < 1e-3)
+    assert_fp64_parity(got, ref, exclude=band, what="per-ray terminating")
+    st = ref["status"][~band]
+    assert (st == oracle.HORIZON).sum() > 5 and (st == oracle.ESCAPED).sum() > 50
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_overflowing_step_is_nonfinite_and_keeps_the_camera_state(tracer, oracle, mode):
+    """A finite but enormous step_precision makes the first step overflow: every ray ends
+    as NONFINITE after 1 step with its initial state, as in the oracle."""
+    for cam in (W.Camera(0.5, 0.0, 0.0, 15.0, 1.2, 75.0, 5, 5),
+                W.Camera(0.5, 0.24, 0.0, 15.0, 1.2, 75.0, 5, 5),
+                W.Camera(0.5, 0.24, 2.0, 15.0, 1.2, 75.0, 5, 5)):
+        got = run_gpu(tracer, cam, 100, 1e200, mode=mode)
+        ref = run_oracle(oracle, cam, 100, 1e200)
+        assert np.all(ref["status"] == oracle.NONFINITE) and np.all(ref["nsteps"] == 1)
+        assert np.array_equal(got["status"], ref["status"])
+        assert np.array_equal(got["nsteps"], ref["nsteps"])
+        for k in ("t", "r", "th", "ph"):
+            assert np.max(np.abs(got[k] - ref[k])) <= 1e-15 * max(1.0, np.max(np.abs(ref[k]))), k

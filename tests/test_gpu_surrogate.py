@@ -132,3 +132,38 @@ def test_train_on_traced_rays_and_gated_inference(g, tracer, oracle):
         assert np.array_equal(got2["status"][~net2], mixed["status"][~net2])
     finally:
         s.close()
+
+
+def test_photon_ring_gate_matches_numpy(g, tracer, oracle):
+    """The Kerr photon-ring gate of gt_surrogate_infer against a numpy evaluation of its
+    stated rule: a pixel falls back when |min_k R(r_k)/(E^2 r_k^4)| < band over the 97
+    geometric radii r_k from 1.0001 r_+ to r0, with E, L and the Carter constant from the
+    pixel's initial momentum (here from the oracle's camera).  With tau = 0 and no
+    direction gate the fallback set is exactly the band; pixels within 1e-9 of the
+    threshold are not judged."""
+    M, a, r0, th0, band = 0.5, 0.45, 15.0, 80 * W.DEG, 0.05
+    cam = W.Camera(M=M, S=a * M, Q=0.0, r0=r0, theta0=th0, fov_deg=75.0, res_x=64, res_y=48)
+    rp = M + math.sqrt(M * M - a * a)
+    rk = np.exp(np.log(rp * 1.0001) + (np.log(r0) - np.log(rp * 1.0001)) * np.arange(97) / 96.0)
+    want, margin = np.zeros(cam.n_rays, bool), np.zeros(cam.n_rays)
+    for j in range(cam.res_y):
+        for i in range(cam.res_x):
+            _, p = oracle.camera_ray(M, a * M, 0.0, r0, th0, 75.0, cam.res_x, cam.res_y, i, j)
+            E, L = -p[0], p[3]
+            K = p[2] ** 2 + math.cos(th0) ** 2 * (-a * a * E * E + L * L / math.sin(th0) ** 2)
+            R = (E * (rk * rk + a * a) - a * L) ** 2 - (rk * rk - 2 * M * rk + a * a) * ((L - a * E) ** 2 + K)
+            v = abs(np.min(R / (E * E * rk ** 4)))
+            want[j * cam.res_x + i] = v < band
+            margin[j * cam.res_x + i] = abs(v - band)
+    s = g.Surrogate(0, seed=5)
+    try:
+        tracer.set_spacetime(cam.M, cam.S, cam.Q)
+        tracer.set_camera(cam.r0, cam.theta0, cam.fov_deg, cam.res_x, cam.res_y)
+        tracer.set_options()
+        out, nfb = s.infer(tracer, tau=0.0, band=band, n_steps=10, step_precision=1.5e-4)
+        got = to_numpy(out)["nsteps"] > 0  # integrated pixels
+        judged = margin > 1e-9
+        assert nfb == got.sum() and 0 < want.sum() < cam.n_rays
+        assert np.array_equal(got[judged], want[judged])
+    finally:
+        s.close()

@@ -95,3 +95,19 @@ def test_invalid_arguments_rejected(oracle, bad):
     with pytest.raises(ValueError):
         oracle.camera_ray(kw["M"], kw["S"], kw["Q"], kw["r0"], kw["th0"], kw["fov"],
                           kw["resX"], kw["resY"], 0, 0)
+
+
+@pytest.mark.parametrize("M,S,Q,r0,th0", CASES)
+def test_direction_camera_is_null_normalised_and_points_where_asked(oracle, M, S, Q, r0, th0):
+    """The per-ray form (direction (alpha, beta) instead of a pixel index, used for the
+    surrogate's training rays): H = 0, v^t = -1, and v^theta/(-v^r) = beta,
+    v^phi sin(theta0)/(-v^r) = alpha, checked with the inverse metric."""
+    rng = np.random.default_rng(4)
+    gu = oracle.metric_upper(M, S, Q, r0, th0)
+    for al, be in rng.uniform(-0.05, 0.05, (20, 2)):
+        q, p = oracle.camera_dir(M, S, Q, r0, th0, al, be)
+        assert list(q) == [0.0, r0, th0, 0.0]
+        v = gu @ p
+        assert abs(v[0] + 1.0) < 1e-13
+        assert abs(0.5 * p @ gu @ p) < 1e-13 * (p @ p)
+        assert abs(v[2] / -v[1] - be) < 1e-13 and abs(v[3] * np.sin(th0) / -v[1] - al) < 1e-13

@@ -91,6 +91,26 @@ def test_noalloc_mixed_mode_within_mixed_tolerance(g):
     assert rep["agree"] >= 0.999 and rep["max_angle_escaped"] <= 1e-3, rep
 
 
+def test_noalloc_mixed_mode_inline_fp64_zone(g):
+    """A Manko-Novikov camera (whose 4M FP64 zone the FP32-mixed kernel enters inline
+    here, converting the ray state to FP64 and back) batched with a Kerr camera, so the
+    per-camera kernel variant runs; against gt_trace_batch's FP64 result with the
+    reduced-precision criteria outside the chaotic boundary band."""
+    cams = [W.Camera(0.5, 0.24, 2.0, 15.0, 80 * W.DEG, 30.0, 10, 8),
+            W.Camera(0.5, 0.24, 0.0, 15.0, 80 * W.DEG, 30.0, 9, 7)]
+    n_steps = 60000
+    got = _noalloc(g, cams, n_steps, 1.5e-4, 1)
+    want = _with_context(g, cams, n_steps, 1.5e-4, 0)
+    offs = np.cumsum([0] + [c.n_rays for c in cams])
+    band = np.concatenate([neighbour_band(want["status"][o:o + c.n_rays], c.res_x, c.res_y)
+                           for c, o in zip(cams, offs)])
+    rep = mixed_report(got, want, exclude=band)
+    assert rep["agree"] >= 0.999 and rep["max_angle_escaped"] <= 1e-3, rep
+    mn = slice(0, cams[0].n_rays)
+    # the MN rays did reach the zone: some were captured or are still inside it
+    assert np.any(want["r"][mn] < 4 * cams[0].M)
+
+
 def test_noalloc_rejects_batches_beyond_its_static_scratch(g):
     lib = g.load_library()
     cams = [W.Camera(0.5, 0.1, 0.0, 12.0, 0.7, 75.0, 2, 2)] * 65

@@ -9,7 +9,8 @@ contraction).  This module only builds it with gcc and marshals arguments
 through ctypes.  Each wrapped C function cites the paper passage it follows
 in the C source.
 
-Status codes: 0 ESCAPED, 1 HORIZON, 2 MAXSTEPS, 3 NONFINITE.
+Status codes: 0 ESCAPED, 1 HORIZON, 2 MAXSTEPS, 3 NONFINITE, 5 DISK (the ray entered the
+ring volume).
 """
 from __future__ import annotations
 
@@ -24,9 +25,12 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "geodesic_oracle.c")
 LIB_PATH = os.path.join(_HERE, "liboracle.so")
 
-ESCAPED, HORIZON, MAXSTEPS, NONFINITE = 0, 1, 2, 3
+ESCAPED, HORIZON, MAXSTEPS, NONFINITE, DISK = 0, 1, 2, 3, 5
 FLAG_COMPAT_WEIGHTS = 1
 FLAG_COMPAT_CAMERA = 2
+FLAG_FD_DERIVS = 4  # forward-difference metric derivatives (listing's derPrecision 1e-8)
+FLAG_F32_IO = 8     # float32 spacetime parameters, initial state and outputs (listing)
+FLAG_EULER = 16     # explicit Euler (Sec. 3.1.1)
 
 _lock = threading.Lock()
 _lib = None
@@ -78,6 +82,13 @@ def _load():
         lib.or_trace_image.argtypes = [d, d, d, d, d, d, i, i, i64, d, i, vp, i64, i,
                                        vp, vp, vp, vp, vp, vp, vp, vp]
         lib.or_trace_image.restype = i
+        lib.or_trace_image_disk.argtypes = [d, d, d, d, d, d, i, i, i64, d, i, d, d, d, vp, i64,
+                                            i, vp, vp, vp, vp, vp, vp, vp]
+        lib.or_trace_image_disk.restype = i
+        lib.or_circular_orbit.argtypes = [d, d, d, d, d, i, pd]
+        lib.or_circular_orbit.restype = i
+        lib.or_redshift.argtypes = [d, d, d, d, d, pd, pd, i, pd]
+        lib.or_redshift.restype = i
         _lib = lib
         return lib
 
@@ -189,6 +200,44 @@ def trace_path(M, S, Q, q, p, r_start, n_steps, sp, flags=0, max_states=None) ->
                                      buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                      max_states, ctypes.byref(n)), "trace_path")
     return buf[: n.value].copy()
+
+
+def circular_orbit(M, S, Q, r, th, flags=0) -> np.ndarray:
+    """Momentum (p_t, p_r, p_theta, p_phi) of the ring's circular-orbit emitter at (r, th)."""
+    p = _arr(4)
+    _check(_load().or_circular_orbit(M, S, Q, r, th, flags, p), "circular_orbit")
+    return np.array(p[:])
+
+
+def redshift(M, S, Q, r0, th0, q, p, flags=0) -> float:
+    """Redshift factor of a ray (q, p) at the ring against a static observer at (r0, th0)."""
+    qa, pa, z = _arr(4), _arr(4), ctypes.c_double()
+    qa[:] = list(map(float, q))
+    pa[:] = list(map(float, p))
+    _check(_load().or_redshift(M, S, Q, r0, th0, qa, pa, flags, ctypes.byref(z)), "redshift")
+    return z.value
+
+
+def trace_image_disk(M, S, Q, r0, th0, fov_deg, resX, resY, n_steps, sp, r_in, r_out,
+                     half_thickness, flags=0, pixels=None, threads=None) -> dict:
+    """trace_image with the ring as an exit; adds the redshift factor "z" per ray."""
+    if threads is None:
+        threads = os.cpu_count() or 1
+    if pixels is not None:
+        pixels = np.ascontiguousarray(pixels, dtype=np.int64)
+        n = pixels.size
+    else:
+        n = int(resX) * int(resY)
+    out = {k: np.zeros(n) for k in ("t", "r", "th", "ph", "z")}
+    out["status"] = np.zeros(n, dtype=np.uint8)
+    out["nsteps"] = np.zeros(n, dtype=np.uint32)
+    rc = _load().or_trace_image_disk(
+        M, S, Q, r0, th0, fov_deg, int(resX), int(resY), int(n_steps), sp, int(flags),
+        r_in, r_out, half_thickness, None if pixels is None else pixels.ctypes.data, int(n),
+        int(threads), *[out[k].ctypes.data for k in ("t", "r", "th", "ph", "status", "nsteps",
+                                                      "z")])
+    _check(rc, "trace_image_disk")
+    return out
 
 
 def trace_image(M, S, Q, r0, th0, fov_deg, resX, resY, n_steps, sp, flags=0,

@@ -24,6 +24,13 @@
  *     when r > 1.5 r_start, horizon when the step falls below
  *     step_precision * 3e-5, otherwise stop after n_steps.
  *
+ *   - the optional paper-numerics variants: forward-difference metric
+ *     derivatives with the listing's derPrecision 1e-8 (three metric
+ *     evaluations per stage), float32 kernel arguments and outputs, and the
+ *     explicit Euler integrator of Sec. 3.1.1;
+ *   - the equatorial ring of Sec. 5's renders as an exit condition and the
+ *     redshift of Sec. 3.3.3 (circular-orbit emitter, static observer).
+ *
  * Derivatives are exact, not finite differences: Kerr uses hand-derived
  * closed forms of d_r, d_theta g^{mu nu}; Manko-Novikov uses complex-step
  * differentiation Im g(x + i h)/h with h = 1e-30 (exact to rounding because
@@ -53,12 +60,18 @@
 #define OR_HORIZON 1
 #define OR_MAXSTEPS 2
 #define OR_NONFINITE 3
+#define OR_DISK 5 /* the ray entered the ring volume */
 
 #define OR_OK 0
 #define OR_ERR_INVALID_ARG (-1)
 
 #define OR_FLAG_COMPAT_WEIGHTS 1 /* RK4 weights 0.1667 as in the listing */
 #define OR_FLAG_COMPAT_CAMERA 2  /* v^phi = alpha (no 1/sin(theta0)) */
+#define OR_FLAG_FD_DERIVS 4      /* forward-difference metric derivatives, derPrecision 1e-8 */
+#define OR_FLAG_F32_IO 8         /* float32 spacetime parameters, initial state and outputs */
+#define OR_FLAG_EULER 16         /* explicit Euler instead of RK4 (Sec. 3.1.1) */
+
+#define OR_FD_DELTA 1e-8 /* the listing's derPrecision */
 
 typedef double complex cplx;
 
@@ -361,12 +374,33 @@ static void metric_dupper(const spacetime *st, double r, double th, double dg[4]
 /* dq^mu = g^{mu nu} p_nu;  dp_mu = -1/2 d_mu g^{nu sigma} p_nu p_sigma.
  * READING: the 1/2 and the minus sign as in Appendix A (the main-text
  * equation drops the 1/2; the listing keeps both). */
-static void vector_field(const spacetime *st, const double q[4], const double p[4],
-                         double dq[4], double dp[4])
+/* Forward differences of the inverse metric as in the listing's propagation kernel:
+ * d_r g^{mu nu} ~ (g^{mu nu}(r + delta, theta) - g^{mu nu}(r, theta))/delta and likewise
+ * in theta, delta = derPrecision = 1e-8; three metric evaluations (the d_t and d_phi
+ * rows are zero for a stationary, axisymmetric metric). */
+static void dupper_fd(const spacetime *st, double r, double th, double dg[4][4][4])
+{
+    double g[4][4], gr[4][4], gt[4][4];
+    metric_upper(st, r, th, g);
+    metric_upper(st, r + OR_FD_DELTA, th, gr);
+    metric_upper(st, r, th + OR_FD_DELTA, gt);
+    memset(dg, 0, 64 * sizeof(double));
+    for (int i = 0; i < 4; i++)
+        for (int j = 0; j < 4; j++) {
+            dg[1][i][j] = (gr[i][j] - g[i][j]) / OR_FD_DELTA;
+            dg[2][i][j] = (gt[i][j] - g[i][j]) / OR_FD_DELTA;
+        }
+}
+
+static void vector_field_f(const spacetime *st, const double q[4], const double p[4],
+                           double dq[4], double dp[4], int flags)
 {
     double g[4][4], dg[4][4][4];
     metric_upper(st, q[1], q[2], g);
-    metric_dupper(st, q[1], q[2], dg);
+    if (flags & OR_FLAG_FD_DERIVS)
+        dupper_fd(st, q[1], q[2], dg);
+    else
+        metric_dupper(st, q[1], q[2], dg);
     for (int mu = 0; mu < 4; mu++) {
         double acc = 0.0;
         for (int nu = 0; nu < 4; nu++)
@@ -378,6 +412,12 @@ static void vector_field(const spacetime *st, const double q[4], const double p[
         for (int nu = 0; nu < 4; nu++) acc += g[mu][nu] * p[nu];
         dq[mu] = acc;
     }
+}
+
+static void vector_field(const spacetime *st, const double q[4], const double p[4],
+                         double dq[4], double dp[4])
+{
+    vector_field_f(st, q, p, dq, dp, 0);
 }
 
 static double hamiltonian(const spacetime *st, const double q[4], const double p[4])
@@ -449,6 +489,85 @@ static int camera_ray(const spacetime *st, double r0, double th0, double fov_deg
 /* RK4 propagation (Sec. 3.1.2, listing's propagation kernel)                */
 /* ------------------------------------------------------------------------ */
 
+/* ------------------------------------------------------------------------ */
+/* Ring and redshift (Sec. 3.3.3; the ring renders of Sec. 5)                */
+/* ------------------------------------------------------------------------ */
+
+/* The ring of the renders: a region around the equator of small, non-zero
+ * thickness (solid, so that a ray stepping into its volume hits it).  READING:
+ * r_in <= r <= r_out and |r cos theta| <= half_thickness. */
+typedef struct {
+    double r_in, r_out, half_thickness;
+} disk_t;
+
+static int in_disk(const disk_t *dk, double r, double th)
+{
+    return r >= dk->r_in && r <= dk->r_out && fabs(r * cos(th)) <= dk->half_thickness;
+}
+
+/* Emitter momentum of the ring at (r, theta) (Sec. 3.3.3): a circular orbit,
+ * p_r = p_theta = 0 and dp_r/dtau = 0, with p_t = -1, so that
+ *     d_r g^{tt} p_t^2 + 2 d_r g^{t phi} p_t p_phi + d_r g^{phi phi} p_phi^2 = 0
+ * (READING: the printed equation has lower indices; the Hamiltonian equation of
+ * motion it is derived from has the inverse metric's derivatives).  Of its two
+ * roots the one with positive angular velocity u^phi/u^t is taken (the ring turns
+ * with +phi, the hole's sense for S > 0; READING), then p is rescaled so that
+ * g^{mu nu} p_mu p_nu = -1.  Returns OR_ERR_INVALID_ARG where no timelike circular
+ * orbit exists (inside the photon orbit). */
+static int circular_orbit(const spacetime *st, double r, double th, int flags, double p[4])
+{
+    double dg[4][4][4], g[4][4];
+    if (flags & OR_FLAG_FD_DERIVS)
+        dupper_fd(st, r, th, dg);
+    else
+        metric_dupper(st, r, th, dg);
+    metric_upper(st, r, th, g);
+    const double A = dg[1][3][3], B = dg[1][0][3], C = dg[1][0][0];
+    /* A p_phi^2 - 2 B p_phi + C = 0 for p_t = -1 */
+    const double disc = B * B - A * C;
+    if (!(disc >= 0.0) || A == 0.0) return OR_ERR_INVALID_ARG;
+    const double roots[2] = {(B + sqrt(disc)) / A, (B - sqrt(disc)) / A};
+    for (int k = 0; k < 2; k++) {
+        const double pph = roots[k];
+        const double ut = -g[0][0] + g[0][3] * pph;
+        const double uph = -g[3][0] + g[3][3] * pph;
+        const double norm = g[0][0] - 2.0 * g[0][3] * pph + g[3][3] * pph * pph;
+        if (ut > 0.0 && uph / ut > 0.0 && norm < 0.0) {
+            const double lam = 1.0 / sqrt(-norm);
+            p[0] = -lam;
+            p[1] = 0.0;
+            p[2] = 0.0;
+            p[3] = lam * pph;
+            return OR_OK;
+        }
+    }
+    return OR_ERR_INVALID_ARG;
+}
+
+/* Redshift factor z = lambda_O / lambda_S = (g_{mu nu} kappa_S^mu S^nu) /
+ * (g_{mu nu} kappa_O^mu O^nu) (Sec. 3.3.3): kappa the traced (backward) ray,
+ * S the ring's 4-velocity at the hit, O the observer's.  READING: the paper makes
+ * the denominator 1 through the v^t = -1 normalisation; here O is the static
+ * observer at the camera, O = (-g_tt(r0, theta0))^(-1/2) d_t, so the denominator
+ * is p_t / sqrt(-g_tt) with p_t conserved along the ray.  NaN where no circular
+ * orbit exists. */
+static double redshift(const spacetime *st, double r0, double th0, const double q[4],
+                       const double p[4], int flags)
+{
+    double pS[4], g[4][4], gl[4][4];
+    if (circular_orbit(st, q[1], q[2], flags, pS) != OR_OK) return NAN;
+    metric_upper(st, q[1], q[2], g);
+    double num = 0.0;
+    for (int mu = 0; mu < 4; mu++) {
+        double u = 0.0;
+        for (int nu = 0; nu < 4; nu++) u += g[mu][nu] * pS[nu];
+        num += p[mu] * u;
+    }
+    metric_lower(st, r0, th0, gl);
+    const double den = p[0] / sqrt(-gl[0][0]);
+    return num / den;
+}
+
 static int all_finite(const double q[4], const double p[4])
 {
     for (int m = 0; m < 4; m++)
@@ -470,7 +589,7 @@ typedef struct {
  * (READING: the paper has no such test).  nsteps counts the terminal step;
  * a ray that never exits is MAXSTEPS with nsteps = n_steps. */
 static void trace_ray(const spacetime *st, double q[4], double p[4], double r_start,
-                      int64_t n_steps, double sp, int flags, ray_result *res)
+                      int64_t n_steps, double sp, int flags, const disk_t *dk, ray_result *res)
 {
     const double w = (flags & OR_FLAG_COMPAT_WEIGHTS) ? 0.1667 : 1.0 / 6.0;
     const double r_escape = 1.5 * r_start;
@@ -478,28 +597,36 @@ static void trace_ray(const spacetime *st, double q[4], double p[4], double r_st
     double xq[4], xp[4];
     double min_sin = fabs(sin(q[2]));
     for (int64_t i = 0; i < n_steps; i++) {
-        vector_field(st, q, p, k1q, k1p);
+        vector_field_f(st, q, p, k1q, k1p, flags);
         const double h = fabs(sp / k1q[0]);
+        double nq[4], np[4];
+        if (flags & OR_FLAG_EULER) { /* Sec. 3.1.1: x += h F(x) */
+            for (int m = 0; m < 4; m++) {
+                nq[m] = q[m] + h * k1q[m];
+                np[m] = p[m] + h * k1p[m];
+            }
+            goto exits;
+        }
         for (int m = 0; m < 4; m++) {
             xq[m] = q[m] + 0.5 * h * k1q[m];
             xp[m] = p[m] + 0.5 * h * k1p[m];
         }
-        vector_field(st, xq, xp, k2q, k2p);
+        vector_field_f(st, xq, xp, k2q, k2p, flags);
         for (int m = 0; m < 4; m++) {
             xq[m] = q[m] + 0.5 * h * k2q[m];
             xp[m] = p[m] + 0.5 * h * k2p[m];
         }
-        vector_field(st, xq, xp, k3q, k3p);
+        vector_field_f(st, xq, xp, k3q, k3p, flags);
         for (int m = 0; m < 4; m++) {
             xq[m] = q[m] + h * k3q[m];
             xp[m] = p[m] + h * k3p[m];
         }
-        vector_field(st, xq, xp, k4q, k4p);
-        double nq[4], np[4];
+        vector_field_f(st, xq, xp, k4q, k4p, flags);
         for (int m = 0; m < 4; m++) {
             np[m] = p[m] + h * w * (k1p[m] + 2.0 * k2p[m] + 2.0 * k3p[m] + k4p[m]);
             nq[m] = q[m] + h * w * (k1q[m] + 2.0 * k2q[m] + 2.0 * k3q[m] + k4q[m]);
         }
+    exits:
         if (!isfinite(h) || !all_finite(nq, np)) {
             res->status = OR_NONFINITE;
             res->nsteps = i + 1;
@@ -512,6 +639,12 @@ static void trace_ray(const spacetime *st, double q[4], double p[4], double r_st
         if (sn < min_sin) min_sin = sn;
         if (q[1] > r_escape) {
             res->status = OR_ESCAPED;
+            res->nsteps = i + 1;
+            res->min_sin = min_sin;
+            return;
+        }
+        if (dk && in_disk(dk, q[1], q[2])) { /* the ring is tested before the horizon */
+            res->status = OR_DISK;
             res->nsteps = i + 1;
             res->min_sin = min_sin;
             return;
@@ -687,7 +820,7 @@ int or_trace_ray(double M, double S, double Q, double *q4, double *p4, double r_
     if (spacetime_init(&st, M, S, Q) != OR_OK) return OR_ERR_INVALID_ARG;
     if (n_steps < 0 || !(sp > 0.0)) return OR_ERR_INVALID_ARG;
     ray_result res;
-    trace_ray(&st, q4, p4, r_start, n_steps, sp, flags, &res);
+    trace_ray(&st, q4, p4, r_start, n_steps, sp, flags, NULL, &res);
     *status = res.status;
     *nsteps = res.nsteps;
     if (min_sin) *min_sin = res.min_sin;
@@ -712,7 +845,7 @@ int or_trace_ray_path(double M, double S, double Q, const double *q4, const doub
     n = 1;
     for (int64_t i = 0; i < n_steps && n < max_states; i++) {
         ray_result res;
-        trace_ray(&st, q, p, r_start, 1, sp, flags, &res);
+        trace_ray(&st, q, p, r_start, 1, sp, flags, NULL, &res);
         if (res.status == OR_NONFINITE) break;
         memcpy(states8 + 8 * n, q, sizeof q);
         memcpy(states8 + 8 * n + 4, p, sizeof p);
@@ -739,7 +872,12 @@ typedef struct {
     double *p_out;   /* optional, 4 per ray */
     double *min_sin; /* optional */
     int err;
+    const disk_t *dk; /* optional ring */
+    double *z;        /* redshift per ray with the ring (NaN where it was not hit) */
 } image_job;
+
+/* float32 rounding of the listing's kernel arguments and outputs (OR_FLAG_F32_IO) */
+static double f32(double v) { return (double)(float)v; }
 
 static void *image_worker(void *arg)
 {
@@ -755,8 +893,18 @@ static void *image_worker(void *arg)
             __atomic_store_n(&job->err, 1, __ATOMIC_RELAXED);
             continue;
         }
+        if (job->flags & OR_FLAG_F32_IO)
+            for (int m = 0; m < 4; m++) {
+                q[m] = f32(q[m]);
+                p[m] = f32(p[m]);
+            }
         ray_result res;
-        trace_ray(job->st, q, p, job->r0, job->n_steps, job->sp, job->flags, &res);
+        trace_ray(job->st, q, p, job->r0, job->n_steps, job->sp, job->flags, job->dk, &res);
+        if (job->z)
+            job->z[k] = res.status == OR_DISK ? redshift(job->st, job->r0, job->th0, q, p, job->flags)
+                                              : NAN;
+        if (job->flags & OR_FLAG_F32_IO)
+            for (int m = 0; m < 4; m++) q[m] = f32(q[m]);
         job->t[k] = q[0];
         job->r[k] = q[1];
         job->th[k] = q[2];
@@ -772,12 +920,18 @@ static void *image_worker(void *arg)
 /* Trace the camera's pixels (all of them when pixels == NULL, else the listed
  * flat indices j*resX + i) on n_threads POSIX threads.  Output k belongs to
  * the k-th traced pixel. */
-int or_trace_image(double M, double S, double Q, double r0, double th0, double fov_deg, int resX,
-                   int resY, int64_t n_steps, double sp, int flags, const int64_t *pixels,
-                   int64_t n_pixels, int n_threads, double *t, double *r, double *th, double *ph,
-                   uint8_t *status, uint32_t *nsteps, double *p_out, double *min_sin)
+static int trace_image(double M, double S, double Q, double r0, double th0, double fov_deg,
+                       int resX, int resY, int64_t n_steps, double sp, int flags,
+                       const int64_t *pixels, int64_t n_pixels, int n_threads, double *t,
+                       double *r, double *th, double *ph, uint8_t *status, uint32_t *nsteps,
+                       double *p_out, double *min_sin, const disk_t *dk, double *z)
 {
     spacetime st;
+    if (flags & OR_FLAG_F32_IO) { /* the listing passes M, S, q as float32 */
+        M = f32(M);
+        S = f32(S);
+        Q = f32(Q);
+    }
     if (spacetime_init(&st, M, S, Q) != OR_OK) return OR_ERR_INVALID_ARG;
     if (!camera_valid(r0, th0, fov_deg, resX, resY)) return OR_ERR_INVALID_ARG;
     if (n_steps < 0 || n_steps > 0xffffffffLL || !(sp > 0.0)) return OR_ERR_INVALID_ARG;
@@ -793,7 +947,7 @@ int or_trace_image(double M, double S, double Q, double r0, double th0, double f
     if (n_threads > 1024) n_threads = 1024;
     image_job job = {&st,   r0,    th0,     fov_deg, resX, resY, n_steps, sp,  flags,
                      pixels, n,    0,       t,       r,    th,   ph,      status, nsteps,
-                     p_out, min_sin, 0};
+                     p_out, min_sin, 0, dk, z};
     pthread_t *tids = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)n_threads);
     if (!tids) return OR_ERR_INVALID_ARG;
     int started = 0;
@@ -805,4 +959,48 @@ int or_trace_image(double M, double S, double Q, double r0, double th0, double f
     for (int k = 0; k < started; k++) pthread_join(tids[k], NULL);
     free(tids);
     return job.err ? OR_ERR_INVALID_ARG : OR_OK;
+}
+
+int or_trace_image(double M, double S, double Q, double r0, double th0, double fov_deg, int resX,
+                   int resY, int64_t n_steps, double sp, int flags, const int64_t *pixels,
+                   int64_t n_pixels, int n_threads, double *t, double *r, double *th, double *ph,
+                   uint8_t *status, uint32_t *nsteps, double *p_out, double *min_sin)
+{
+    return trace_image(M, S, Q, r0, th0, fov_deg, resX, resY, n_steps, sp, flags, pixels,
+                       n_pixels, n_threads, t, r, th, ph, status, nsteps, p_out, min_sin, NULL,
+                       NULL);
+}
+
+/* As or_trace_image with the ring r_in <= r <= r_out, |r cos theta| <= half_thickness
+ * as an exit (status 5, tested after the escape and before the horizon) and the
+ * redshift factor of each ray that hit it in z (NaN otherwise). */
+int or_trace_image_disk(double M, double S, double Q, double r0, double th0, double fov_deg,
+                        int resX, int resY, int64_t n_steps, double sp, int flags, double r_in,
+                        double r_out, double half_thickness, const int64_t *pixels,
+                        int64_t n_pixels, int n_threads, double *t, double *r, double *th,
+                        double *ph, uint8_t *status, uint32_t *nsteps, double *z)
+{
+    if (!(r_in > 0.0) || !(r_out > r_in) || !(half_thickness > 0.0) || !z) return OR_ERR_INVALID_ARG;
+    const disk_t dk = {r_in, r_out, half_thickness};
+    return trace_image(M, S, Q, r0, th0, fov_deg, resX, resY, n_steps, sp, flags, pixels,
+                       n_pixels, n_threads, t, r, th, ph, status, nsteps, NULL, NULL, &dk, z);
+}
+
+/* Ring emitter momentum (p_t, p_r, p_theta, p_phi) at (r, theta). */
+int or_circular_orbit(double M, double S, double Q, double r, double th, int flags, double *p4)
+{
+    spacetime st;
+    if (spacetime_init(&st, M, S, Q) != OR_OK || !p4) return OR_ERR_INVALID_ARG;
+    return circular_orbit(&st, r, th, flags, p4);
+}
+
+/* Redshift factor of a ray with momentum p4 at position q4 against a static observer
+ * at (r0, th0). */
+int or_redshift(double M, double S, double Q, double r0, double th0, const double *q4,
+                const double *p4, int flags, double *z)
+{
+    spacetime st;
+    if (spacetime_init(&st, M, S, Q) != OR_OK || !q4 || !p4 || !z) return OR_ERR_INVALID_ARG;
+    *z = redshift(&st, r0, th0, q4, p4, flags);
+    return OR_OK;
 }

@@ -8,12 +8,14 @@ layers 16 -> 256 -> 256 -> 256 -> 256 -> 16 with SiLU between them, output
 (escape logit, end-direction vector, 12 unused), loss
     mean( BCE(logit, y) + w * y * |d_pred - d|^2 ),
 where y = 1 for escaped rays and d = (sin th cos ph, sin th sin ph, cos th) of the end
-position.  With `bf=True` the values are rounded where the GPU stores them in 16 bits:
-to IEEE half precision for the forward products (layer inputs and weights) and to
-bfloat16 for the backward products (the transposed layer inputs of the weight gradient,
-the weights of the input gradient and the gradients themselves), both round to nearest
-even, so that GPU and CPU gradients can be compared closely; with `bf=False` it is the
-exact FP64 network, whose gradient a finite-difference test pins.
+position.  With `bf=True` the values are rounded where the GPU stores them in 16 bits,
+round to nearest even: each forward product is split-precision bfloat16 -- the layer
+input, rounded to float32 as the GPU holds it, and the weight are each carried as a pair
+hi = bf16(v), lo = bf16(v - hi), and the product is x_hi w_hi + x_lo w_hi + x_hi w_lo --
+and the backward products take bfloat16 operands (the transposed layer inputs of the
+weight gradient, the weights of the input gradient and the gradients themselves), so
+that GPU and CPU results can be compared closely; with `bf=False` it is the exact FP64
+network, whose gradient a finite-difference test pins.
 """
 from __future__ import annotations
 
@@ -46,11 +48,6 @@ def bf16(x) -> np.ndarray:
     u = f.view(np.uint32).astype(np.uint64)
     u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
-
-
-def f16(x) -> np.ndarray:
-    """Round to IEEE binary16 (nearest even); returned as float64."""
-    return np.asarray(x, dtype=np.float64).astype(np.float16).astype(np.float64)
 
 
 def features(alpha, beta, spin, q, theta0, r0=15.0, fov_deg=75.0, spin_max=0.99, q_max=2.0,
@@ -90,14 +87,32 @@ def dsilu(z):
     return s * (1 + z * (1 - s))
 
 
+def split_bf16(x):
+    """The bf16 pair (hi, lo) of x as the GPU forms it: x rounded to float32, hi = bf16(x),
+    lo = bf16(x - hi) (the difference is exact in float32); hi + lo carries x to about
+    2^-17 relative."""
+    x32 = np.asarray(x, dtype=np.float32).astype(np.float64)
+    hi = bf16(x32)
+    return hi, bf16(x32 - hi)
+
+
+def split_product(A, W):
+    """A W^T by the split-precision rule x_hi w_hi + x_lo w_hi + x_hi w_lo."""
+    a_hi, a_lo = split_bf16(A)
+    w_hi, w_lo = split_bf16(W)
+    return a_hi @ w_hi.T + a_lo @ w_hi.T + a_hi @ w_lo.T
+
+
 def forward(params, X0, bf=True):
     """Returns the unrounded layer inputs A[0..4] and the pre-activations Z[0..4]; with
-    bf=True each product takes half-precision inputs and weights."""
-    h = f16 if bf else (lambda a: np.asarray(a, dtype=np.float64))
+    bf=True each product is the split-precision bf16 product of the GPU."""
     ws, bs = split(params)
     As, Zs = [np.asarray(X0, dtype=np.float64)], []
     for l in range(5):
-        Z = h(As[-1]) @ h(ws[l]).T + bs[l]
+        if bf:
+            Z = split_product(As[-1], ws[l]) + bs[l]
+        else:
+            Z = As[-1] @ ws[l].T + bs[l]
         Zs.append(Z)
         if l < 4:
             As.append(silu(Z))

@@ -112,6 +112,28 @@ __device__ __forceinline__ uint32_t pack_c16(float lo, float hi, int f16)
     return *reinterpret_cast<const uint32_t *>(&h);
 }
 
+// bf16 pair of y: hi = bf16(y) and lo = bf16(y - hi) (y - hi is exact in FP32), so that
+// hi + lo carries y to about 2^-17 relative
+__device__ __forceinline__ void split_bf16(float y, __nv_bfloat16 *hi, __nv_bfloat16 *lo)
+{
+    *hi = __float2bfloat16(y);
+    *lo = __float2bfloat16(y - __bfloat162float(*hi));
+}
+
+// One 16-bit output value: plain, or split into [hi | lo | hi] columns (c16_split)
+__device__ __forceinline__ void store_c16(const GemmArgs &g, int64_t row, int col, float y)
+{
+    __nv_bfloat16 *p = g.C16 + row * g.ldc16 + col;
+    if (g.c16_split) {
+        __nv_bfloat16 hi, lo;
+        split_bf16(y, &hi, &lo);
+        p[0] = hi;
+        p[g.N] = lo;
+        p[2 * g.N] = hi;
+    } else {
+        *p = to_c16(y, g.c16_f16);
+    }
+}
 
 // Epilogue shared by both kernels: TMEM -> registers (thread = row) -> bias -> shared
 // memory tile (32 columns at a time) -> coalesced stores where each warp writes
@@ -157,7 +179,7 @@ __device__ __forceinline__ void gemm_epilogue(const GemmArgs &g, uint32_t tmem, 
                     else
                         *p = y;
                 }
-                if (g.C16) g.C16[(int64_t)row * g.ldc16 + col] = to_c16(y, g.c16_f16);
+                if (g.C16) store_c16(g, row, col, y);
             }
         }
         __syncthreads();
@@ -590,19 +612,32 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
                         tc::bulk_commit();
                     }
                 }
-                if (g.C16) { // 16-bit box, row = lane (64 bytes), chunk c at c ^ ((row / 2) % 4)
+                // 16-bit box, row = lane (64 bytes), chunk c at c ^ ((row / 2) % 4); with
+                // c16_split the hi halves first (the lo halves follow below)
+                auto put_b16 = [&](bool lo_part) {
 #pragma unroll
                     for (int c = 0; c < 4; c++) {
                         uint4 w;
                         uint32_t *wp = &w.x;
 #pragma unroll
                         for (int j = 0; j < 4; j++) {
-                            wp[j] = pack_c16(v[8 * c + 2 * j], v[8 * c + 2 * j + 1], g.c16_f16);
+                            const float a = v[8 * c + 2 * j], b = v[8 * c + 2 * j + 1];
+                            if (g.c16_split) {
+                                __nv_bfloat16 ha, la, hb, lb;
+                                split_bf16(a, &ha, &la);
+                                split_bf16(b, &hb, &lb);
+                                const __nv_bfloat162 h2 = lo_part ? __halves2bfloat162(la, lb)
+                                                                  : __halves2bfloat162(ha, hb);
+                                wp[j] = *reinterpret_cast<const uint32_t *>(&h2);
+                            } else {
+                                wp[j] = pack_c16(a, b, g.c16_f16);
+                            }
                         }
                         *reinterpret_cast<uint4 *>(stg + STG_B16 + lane * 64 +
                                                    ((c ^ ((lane >> 1) & 3)) << 4)) = w;
                     }
-                }
+                };
+                if (g.C16) put_b16(false);
                 if (g.C16T) { // transposed bf16 box: row = column i, element = lane
 #pragma unroll
                     for (int i = 0; i < 32; i++)
@@ -614,7 +649,19 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
                     __syncwarp();
                     if (lane == 0) {
                         if (g.C16) tc::tma_store_2d(&om.c16, n0 + cc, m0, s_b16);
+                        if (g.C16 && g.c16_split) tc::tma_store_2d(&om.c16, 2 * g.N + n0 + cc, m0, s_b16);
                         if (g.C16T) tc::tma_store_2d(&om.c16t, m0, n0 + cc, s_b16t);
+                        tc::bulk_commit();
+                    }
+                }
+                if (g.C16 && g.c16_split) { // the lo halves into the middle N columns
+                    if (lane == 0) tc::bulk_wait_read();
+                    __syncwarp();
+                    put_b16(true);
+                    tc::fence_proxy_async();
+                    __syncwarp();
+                    if (lane == 0) {
+                        tc::tma_store_2d(&om.c16, g.N + n0 + cc, m0, s_b16);
                         tc::bulk_commit();
                     }
                 }
@@ -674,7 +721,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
                                 else
                                     *p = y;
                             }
-                            if (g.C16) g.C16[row * g.ldc16 + col] = to_c16(y, g.c16_f16);
+                            if (g.C16) store_c16(g, row, col, y);
                         }
                     }
                 }
@@ -773,7 +820,7 @@ cudaError_t launch_ws(const GemmArgs &g, int splits, cudaStream_t s, bool *used)
     if (tma_out && g.C16)
         tma_out = make_out_map(&om.c16, g.C16,
                                g.c16_f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
-                               2, g.M, g.N,
+                               2, g.M, g.c16_split ? 3 * (uint64_t)g.N : (uint64_t)g.N,
                                g.ldc16, CU_TENSOR_MAP_SWIZZLE_64B);
     if (tma_out && g.C16T)
         tma_out = make_out_map(&om.c16t, g.C16T, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, g.N, g.M, g.ldt,

@@ -27,6 +27,9 @@ struct GemmArgs {
     int *err;          // set to 1 when an mbarrier wait ran out
     int f16_in;        // A and B hold IEEE fp16 bit patterns instead of bf16 (both, never mixed)
     int c16_f16;       // C16 receives fp16 instead of bf16 (C16T stays bf16)
+    int c16_split;     // C16 receives each value y as a bf16 pair (hi, lo), hi = bf16(y),
+                       // lo = bf16(y - hi), laid out [hi | lo | hi] over 3 N columns
+                       // (ldc16 >= 3 N): the A operand of a split-precision product
 };
 
 // bn in {16, 32, 64, 128, 256}; splits = K splits (gridDim.z).

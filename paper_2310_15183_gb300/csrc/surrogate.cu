@@ -4,13 +4,17 @@
 // low-confidence and photon-ring pixels.
 //
 // Network: 16 (5 inputs and 5 columns derived from them, zero padded) -> 256 -> 256 ->
-// 256 -> 256 -> 16 (4 used:
-// logit and the unit vector of the end direction, which unlike (theta, phi) has no
-// jump at phi = +-pi), SiLU between layers.  FP32 master weights and AdamW state.
-// The forward products take FP16 weights and activations (10-bit mantissa: the end
-// direction is read from the last layer, and BF16's 7 bits put a rounding floor of about
-// 2e-3 rad under it); the backward products take BF16, whose range holds gradients
-// scaled by 1/batch.  Accumulation is FP32 throughout.
+// 256 -> 256 -> 16 (4 used: logit and the unit vector of the end direction, which unlike
+// (theta, phi) has no jump at phi = +-pi), SiLU between layers.  FP32 master weights and
+// AdamW state.  The forward products are split-precision BF16: each layer input x and
+// weight w is carried as a bf16 pair (hi, lo), hi = bf16(v), lo = bf16(v - hi), and the
+// product is x_hi w_hi + x_lo w_hi + x_hi w_lo -- one tcgen05 GEMM over K' = 3K with the
+// input laid out [x_hi | x_lo | x_hi] and the weights [w_hi | w_hi | w_lo] -- which carries
+// the layer to about 2^-16 relative instead of bf16's 2^-8 (the dropped x_lo w_lo term is
+// 2^-16 of the product); the end direction is read from the last layer, and a single
+// 16-bit product leaves a rounding floor of 5e-4 (FP16) to 2e-3 rad (BF16) under it.  The
+// backward products take plain BF16, whose range holds gradients scaled by 1/batch.
+// Accumulation is FP32 throughout.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -85,19 +89,39 @@ __device__ __forceinline__ void make_features(double al, double bt, double spin,
     for (int j = 10; j < 16; j++) f[j] = 0.0f;
 }
 
-// features of samples [row0, row0 + n): X0[r, 0..15] (fp16, input of the forward
-// product) and optionally X0T (bf16, transposed, input of the weight-gradient product)
+// bf16 pair of v: hi = bf16(v), lo = bf16(v - hi)
+__device__ __forceinline__ void split_pair(float v, __nv_bfloat16 *hi, __nv_bfloat16 *lo)
+{
+    *hi = __float2bfloat16(v);
+    *lo = __float2bfloat16(v - __bfloat162float(*hi));
+}
+
+// One row of the first layer's split input: columns [hi 0..15 | lo 0..15 | hi 0..15]
+__device__ __forceinline__ void store_split_row(const float f[16], __nv_bfloat16 *row)
+{
+#pragma unroll
+    for (int j = 0; j < 16; j++) {
+        __nv_bfloat16 hi, lo;
+        split_pair(f[j], &hi, &lo);
+        row[j] = hi;
+        row[16 + j] = lo;
+        row[32 + j] = hi;
+    }
+}
+
+// features of samples [row0, row0 + n): X0[r, 0..47] (split bf16, input of the forward
+// product) and optionally X0T (bf16 of the features, transposed, input of the
+// weight-gradient product)
 __global__ void features_kernel(int64_t n, int64_t row0, const double *alpha, const double *beta,
                                 const double *spin, const double *q, const double *theta0,
-                                Norm nm, __half *X0, __nv_bfloat16 *X0T = nullptr)
+                                Norm nm, __nv_bfloat16 *X0, __nv_bfloat16 *X0T = nullptr)
 {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     const int64_t k = row0 + r;
     float f[16];
     make_features(alpha[k], beta[k], spin[k], q[k], theta0[k], nm, f);
-#pragma unroll
-    for (int j = 0; j < 16; j++) X0[r * 16 + j] = __float2half_rn(f[j]);
+    store_split_row(f, X0 + r * 3 * 16);
     if (X0T)
 #pragma unroll
         for (int j = 0; j < 16; j++) X0T[j * n + r] = __float2bfloat16(f[j]);
@@ -105,7 +129,7 @@ __global__ void features_kernel(int64_t n, int64_t row0, const double *alpha, co
 
 // features of camera pixels [pix0, pix0 + n) (flat j*res_x + i)
 __global__ void camera_features_kernel(int64_t n, int64_t pix0, const CamDesc *cam, Norm nm,
-                                       __half *X0)
+                                       __nv_bfloat16 *X0)
 {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
@@ -116,8 +140,7 @@ __global__ void camera_features_kernel(int64_t n, int64_t pix0, const CamDesc *c
     const double bt = c.res_y > 1 ? c.V * (double)(2 * j - (c.res_y - 1)) / (double)(c.res_y - 1) : 0.0;
     float f[16];
     make_features(al, bt, (c.S / c.M) / c.M, c.Q, c.th0, nm, f);
-#pragma unroll
-    for (int jj = 0; jj < 16; jj++) X0[r * 16 + jj] = __float2half_rn(f[jj]);
+    store_split_row(f, X0 + r * 3 * 16);
 }
 
 // Loss of rows [0, B): BCE(logit, y) + w_dir * y * |d_pred - d|^2, averaged over B.
@@ -211,10 +234,19 @@ __global__ void adamw_kernel(int64_t n, float *p, const float *g, float *m, floa
     p[i] = pi;
 }
 
-__global__ void to_f16_kernel(int64_t n, const float *src, __half *dst)
+// W3 = [w_hi | w_hi | w_lo] per output row (bf16, [out][3 in]) of fp32 weights [out][in]:
+// the B operand of the split-precision forward product
+__global__ void weights_split_kernel(const float *W, int out_dim, int in_dim, __nv_bfloat16 *W3)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = __float2half_rn(src[i]);
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= out_dim * in_dim) return;
+    const int o = k / in_dim, i = k % in_dim;
+    __nv_bfloat16 hi, lo;
+    split_pair(W[k], &hi, &lo);
+    __nv_bfloat16 *row = W3 + (int64_t)o * 3 * in_dim;
+    row[i] = hi;
+    row[in_dim + i] = hi;
+    row[2 * in_dim + i] = lo;
 }
 
 // Photon-ring test for a Kerr pixel: with E = -p_t, L = p_phi and the Carter constant
@@ -332,11 +364,12 @@ struct gt_surrogate {
     int64_t n_params = 0;
     float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr; // fp32 params, grads, Adam
     uint8_t *decay = nullptr;
-    __half *wh = nullptr; // fp16 copy of all params for the forward products (weights only)
+    __nv_bfloat16 *w3 = nullptr; // split bf16 weights of the forward products, [out][3 in] per layer
+    int64_t w3_off[N_LAYERS] = {};
     int64_t step = 0;
     // workspace for `rows` rows
     int64_t rows = 0;
-    __half *X[N_LAYERS] = {};         // inputs of each layer (fp16, forward products)
+    __nv_bfloat16 *X[N_LAYERS] = {};  // split inputs of each layer (rows x 3 in, forward products)
     __nv_bfloat16 *XT[N_LAYERS] = {}; // the same in bf16, transposed (in_dim x rows)
     __nv_bfloat16 *WT = nullptr;      // transposed bf16 weights ([in][out] per layer)
     __nv_bfloat16 *dZT = nullptr;     // transposed bf16 gradient (cols x rows)
@@ -375,7 +408,7 @@ int ensure_ws(gt_surrogate *s, int64_t rows)
     free_ws(s);
     cudaError_t e = cudaSuccess;
     for (int l = 0; l < N_LAYERS && e == cudaSuccess; l++) {
-        e = cudaMalloc(&s->X[l], rows * IN_DIM[l] * sizeof(__half));
+        e = cudaMalloc(&s->X[l], rows * 3 * IN_DIM[l] * sizeof(__nv_bfloat16));
         if (e == cudaSuccess) e = cudaMalloc(&s->XT[l], rows * IN_DIM[l] * sizeof(__nv_bfloat16));
         if (e == cudaSuccess) e = cudaMalloc(&s->Z[l], rows * OUT_DIM[l] * sizeof(float));
     }
@@ -406,15 +439,14 @@ struct Dev {
     }
 };
 
-// f16: A, B and C16 are fp16 (the forward products); otherwise bf16.  C16T is bf16.
+// split: C16 receives the [hi | lo | hi] split of the output (3 N columns)
 cudaError_t gemm(const void *A, int64_t a_sm, int64_t a_sk, const void *B, int64_t b_sn,
                  int64_t b_sk, int M, int N, int K, const float *bias, int act, float *pre,
                  float *C32, int64_t ldc, bool atomic, void *C16, int splits, int *err,
-                 cudaStream_t st, __nv_bfloat16 *C16T = nullptr, bool f16 = false)
+                 cudaStream_t st, __nv_bfloat16 *C16T = nullptr, bool split = false)
 {
     GemmArgs g = {};
-    g.f16_in = f16 ? 1 : 0;
-    g.c16_f16 = f16 ? 1 : 0;
+    g.c16_split = split ? 1 : 0;
     g.M = M;
     g.N = N;
     g.K = K;
@@ -432,7 +464,7 @@ cudaError_t gemm(const void *A, int64_t a_sm, int64_t a_sk, const void *B, int64
     g.ldc = ldc;
     g.atomic = atomic ? 1 : 0;
     g.C16 = static_cast<__nv_bfloat16 *>(C16);
-    g.ldc16 = N;
+    g.ldc16 = split ? 3 * (int64_t)N : N;
     g.C16T = C16T;
     g.ldt = M;
     g.err = err;
@@ -449,7 +481,8 @@ cudaError_t forward(gt_surrogate *s, int B, cudaStream_t st, bool keep_pre = tru
     cudaError_t e = cudaSuccess;
     for (int l = 0; l < N_LAYERS && e == cudaSuccess; l++) {
         const bool last = (l == N_LAYERS - 1);
-        e = gemm(s->X[l], IN_DIM[l], 1, s->wh + s->w_off[l], IN_DIM[l], 1, B, OUT_DIM[l], IN_DIM[l],
+        const int K3 = 3 * IN_DIM[l];
+        e = gemm(s->X[l], K3, 1, s->w3 + s->w3_off[l], K3, 1, B, OUT_DIM[l], K3,
                  s->p + s->b_off[l], last ? 0 : 1, (last || !keep_pre) ? nullptr : s->Z[l],
                  last ? s->Z[l] : nullptr, OUT_DIM[l], false, last ? nullptr : s->X[l + 1], 1,
                  s->err, st, (last || !keep_pre) ? nullptr : s->XT[l + 1], true);
@@ -495,14 +528,17 @@ int check_err(gt_surrogate *s, cudaStream_t st)
     return h ? GT_ERR_TIMEOUT : GT_OK;
 }
 
-// fp16 copy of the parameters (forward products) and transposed bf16 weights (backward
-// products) after an update
+// split bf16 weights (forward products) and transposed bf16 weights (backward products)
+// after an update
 cudaError_t refresh_copies(gt_surrogate *s, cudaStream_t st)
 {
-    to_f16_kernel<<<blocks_for(s->n_params), 256, 0, st>>>(s->n_params, s->p, s->wh);
-    for (int l = 0; l < N_LAYERS; l++)
-        weights_t_kernel<<<blocks_for((int64_t)OUT_DIM[l] * IN_DIM[l]), 256, 0, st>>>(
-            s->p + s->w_off[l], OUT_DIM[l], IN_DIM[l], s->WT + s->w_off[l]);
+    for (int l = 0; l < N_LAYERS; l++) {
+        const int64_t n = (int64_t)OUT_DIM[l] * IN_DIM[l];
+        weights_split_kernel<<<blocks_for(n), 256, 0, st>>>(s->p + s->w_off[l], OUT_DIM[l],
+                                                           IN_DIM[l], s->w3 + s->w3_off[l]);
+        weights_t_kernel<<<blocks_for(n), 256, 0, st>>>(s->p + s->w_off[l], OUT_DIM[l], IN_DIM[l],
+                                                        s->WT + s->w_off[l]);
+    }
     return cudaGetLastError();
 }
 
@@ -566,7 +602,12 @@ int gt_surrogate_create(int device, const gt_surrogate_norm *nrm, uint64_t seed,
     if (e == cudaSuccess) e = cudaMalloc(&s->g, off * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&s->m, off * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&s->v, off * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&s->wh, off * sizeof(__half));
+    int64_t off3 = 0;
+    for (int l = 0; l < N_LAYERS; l++) {
+        s->w3_off[l] = off3;
+        off3 += (int64_t)OUT_DIM[l] * 3 * IN_DIM[l];
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&s->w3, off3 * sizeof(__nv_bfloat16));
     if (e == cudaSuccess) e = cudaMalloc(&s->WT, off * sizeof(__nv_bfloat16));
     if (e == cudaSuccess) e = cudaMalloc(&s->decay, off);
     if (e == cudaSuccess) e = cudaMalloc(&s->loss, sizeof(float));
@@ -606,7 +647,7 @@ int gt_surrogate_destroy(gt_surrogate *s)
     cudaFree(s->g);
     cudaFree(s->m);
     cudaFree(s->v);
-    cudaFree(s->wh);
+    cudaFree(s->w3);
     cudaFree(s->WT);
     cudaFree(s->decay);
     cudaFree(s->loss);

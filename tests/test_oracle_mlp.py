@@ -54,23 +54,19 @@ def test_features_cover_unit_range():
     assert np.allclose(X[:, 8] ** 2 + X[:, 9] ** 2, 1.0) and np.all(X[:, 10:] == 0)
 
 
-def test_f16_rounding_is_round_to_nearest_even():
-    x = np.array([1.0, 1.0 + 2 ** -11, 1.0 + 3 * 2 ** -11, 1.0 + 2 ** -10, -2.5, 65504.0])
-    r = mlp.f16(x)
-    assert r[0] == 1.0 and r[1] == 1.0 and r[2] == 1.0 + 2 ** -9
-    assert r[3] == 1.0 + 2 ** -10 and r[4] == -2.5 and r[5] == 65504.0
-
-
-def test_rounded_network_stays_close_to_exact():
-    """The 16-bit rounding points perturb the loss and gradient only slightly (a
-    transposed or misplaced rounding would not)."""
-    p = mlp.init_params(4)
-    rng = np.random.Generator(np.random.PCG64(8))
-    X0 = mlp.features(rng.uniform(-0.04, 0.04, 64), rng.uniform(-0.04, 0.04, 64),
-                      rng.uniform(0, 0.99, 64), np.zeros(64), rng.uniform(0.1, 1.5, 64))
-    y = (rng.uniform(size=64) < 0.5).astype(float)
-    d = np.stack([np.ones(64), np.zeros(64), np.zeros(64)], 1) * y[:, None]
-    l0, g0, _ = mlp.loss_and_grad(p, X0, y, d, 10.0, bf=False)
-    l1, g1, _ = mlp.loss_and_grad(p, X0, y, d, 10.0, bf=True)
-    assert abs(l1 - l0) < 1e-2 * abs(l0)
-    assert np.linalg.norm(g1 - g0) < 2e-2 * np.linalg.norm(g0)
+def test_split_product_error_bound():
+    """The split-precision product x_hi w_hi + x_lo w_hi + x_hi w_lo (hi = bf16(v),
+    lo = bf16(v - hi)) is within 2^-15 sum_k |x_k||w_k| of the exact product: each pair
+    carries its value to 2^-17 and the dropped x_lo w_lo is at most 2^-16 of |x||w|.
+    A single bf16 product is not (its error is ~2^-9)."""
+    rng = np.random.default_rng(8)
+    A = rng.normal(0, 1, (64, 256)) * np.exp(rng.uniform(-3, 3, (64, 1)))
+    Wt = rng.normal(0, 0.06, (48, 256))
+    exact = A @ Wt.T
+    scale = np.abs(A) @ np.abs(Wt).T
+    err = np.abs(mlp.split_product(A, Wt) - exact)
+    assert np.all(err <= 2.0 ** -15 * scale)
+    plain = np.abs(mlp.bf16(A) @ mlp.bf16(Wt).T - exact)
+    assert np.max(plain / scale) > 2.0 ** -11
+    hi, lo = mlp.split_bf16(A)
+    assert np.all(np.abs(hi + lo - A) <= 2.0 ** -16 * np.abs(A))

@@ -98,7 +98,7 @@ def test_noalloc_mixed_mode_inline_fp64_zone(g):
     reduced-precision criteria outside the chaotic boundary band."""
     cams = [W.Camera(0.5, 0.24, 2.0, 15.0, 80 * W.DEG, 30.0, 10, 8),
             W.Camera(0.5, 0.24, 0.0, 15.0, 80 * W.DEG, 30.0, 9, 7)]
-    n_steps = 60000
+    n_steps = 200000
     got = _noalloc(g, cams, n_steps, 1.5e-4, 1)
     want = _with_context(g, cams, n_steps, 1.5e-4, 0)
     offs = np.cumsum([0] + [c.n_rays for c in cams])
@@ -108,7 +108,7 @@ def test_noalloc_mixed_mode_inline_fp64_zone(g):
     assert rep["agree"] >= 0.999 and rep["max_angle_escaped"] <= 1e-3, rep
     mn = slice(0, cams[0].n_rays)
     # the MN rays did reach the zone: some were captured or are still inside it
-    assert np.any(want["r"][mn] < 4 * cams[0].M)
+    assert np.any((want["status"][mn] == 1) | (want["r"][mn] < 4 * cams[0].M))
 
 
 def test_noalloc_rejects_batches_beyond_its_static_scratch(g):

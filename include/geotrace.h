@@ -56,6 +56,7 @@ extern "C" {
 #define GT_RAY_MAXSTEPS 2
 #define GT_RAY_NONFINITE 3
 #define GT_RAY_TIMEOUT 4
+#define GT_RAY_DISK 5 /* entered the ring volume (gt_trace_disk) */
 
 /* arithmetic modes */
 #define GT_MODE_FP64 0       /* FP64 end to end */
@@ -76,6 +77,15 @@ extern "C" {
                                   * sums as closed-form series tails, free of the cancellation
                                   * that costs the plain FP32 form ~2 beta ulp(1) in its
                                   * exponents (about 100x closer to FP64; ~20 % slower) */
+/* The paper's own numerics (appendix listing, propagation kernel), GT_MODE_FP64 only;
+ * with GT_FLAG_COMPAT_WEIGHTS and GT_FLAG_COMPAT_CAMERA they reproduce the listing. */
+#define GT_FLAG_FD_DERIVS 32     /* forward-difference metric derivatives with the listing's
+                                  * derPrecision 1e-8: three evaluations of g^{mu nu} per RK4
+                                  * stage instead of the exact derivatives */
+#define GT_FLAG_F32_IO 64        /* float32 kernel arguments and results as in the listing:
+                                  * M, S, Q, the camera's initial state and the end position
+                                  * t, r, theta, phi rounded to float32 (arithmetic in FP64) */
+#define GT_FLAG_EULER 128        /* explicit Euler (Sec. 3.1.1) instead of RK4, same step rule */
 
 typedef struct gt_ctx gt_ctx;
 
@@ -174,6 +184,36 @@ int gt_trace_rays(gt_ctx *ctx, int64_t n, const double *alpha, const double *bet
                   const double *spin, const double *q, const double *theta0, double M, double r0,
                   int64_t n_steps, double step_precision, int mode, double *t, double *r,
                   double *theta, double *phi, uint8_t *status, uint32_t *nsteps);
+
+/* The paper's ring (Sec. 3.3.3 "Redshift"; the ring renders of Sec. 5): as gt_trace, with
+ * the region r_in <= r <= r_out, |r cos theta| <= half_thickness (a solid ring around the
+ * equator; 0 < r_in < r_out, half_thickness > 0) as an extra exit, tested after every step
+ * after the escape test and before the horizon test.  Rays that enter it end with status
+ * GT_RAY_DISK and get the redshift factor z = lambda_O / lambda_S =
+ * (p . u_S) / (p . u_O): u_S the 4-velocity of a ring element on the circular orbit through
+ * the hit point (p_r = p_theta = 0, dp_r/dtau = 0, p_t = -1, the prograde root, normalised
+ * to g^{mu nu} p_mu p_nu = -1), u_O the static observer at the camera.  z (a DEVICE float64
+ * array of res_x*res_y elements, 8-byte aligned) is NaN for the other rays and where no
+ * timelike circular orbit exists.  Other outputs and errors as gt_trace, plus
+ * GT_ERR_INVALID_ARG for a bad ring or z == NULL. */
+int gt_trace_disk(gt_ctx *ctx, double r_in, double r_out, double half_thickness, int64_t n_steps,
+                  double step_precision, int mode, double *t, double *r, double *theta,
+                  double *phi, uint8_t *status, uint32_t *nsteps, double *z);
+
+/* Integrate n rays (or massive particles) of the configured spacetime from arbitrary
+ * states: SoA DEVICE float64 arrays t, r, theta, phi, p_t, p_r, p_theta, p_phi of n
+ * elements hold the initial state and receive the end state (in place).  Null rays
+ * have g^{mu nu} p_mu p_nu = 0, timelike orbits -1 (Sec. 3.2.1 "Orbits": H = -1/2); the
+ * step rule and exit tests are gt_trace's with the escape radius r_escape (> 0).  A ray
+ * that stopped at MAXSTEPS continues from its returned state on the next call: the
+ * state is the whole integrator state, so n1 steps followed by n2 steps give the same
+ * bits as n1 + n2 steps in one call (GT_MODE_FP64) -- a checkpoint.  status and nsteps
+ * (steps of this call) as gt_trace, optional.  No camera is needed.  Errors:
+ * GT_ERR_NOT_CONFIGURED (no spacetime), GT_ERR_INVALID_ARG, GT_ERR_CUDA. */
+int gt_trace_states(gt_ctx *ctx, int64_t n, double *t, double *r, double *theta, double *phi,
+                    double *p_t, double *p_r, double *p_theta, double *p_phi, double r_escape,
+                    int64_t n_steps, double step_precision, int mode, uint8_t *status,
+                    uint32_t *nsteps);
 
 /* ---------------------------------------------------------------------------------
  * Surrogate: an MLP (alpha, beta, spin a/M, q, theta0) -> (escape logit, unit end

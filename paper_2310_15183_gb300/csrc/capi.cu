@@ -51,6 +51,8 @@ struct gt_ctx {
     gt::ParkItem *graph_park = nullptr;
     // per-ray parameter block (gt_trace_rays) and surrogate fallback list
     gt::RayParams *d_rays = nullptr;
+    // spacetime descriptor of gt_trace_states (no camera)
+    CamDesc *d_state_cam = nullptr;
     int64_t *d_fallback = nullptr;
     int64_t fallback_cap = 0;
 };
@@ -84,7 +86,12 @@ struct DeviceGuard {
 int cuda_code(cudaError_t e)
 {
     if (e == cudaSuccess) return GT_OK;
-    if (e == cudaErrorMemoryAllocation) return GT_ERR_OOM;
+    if (e == cudaErrorMemoryAllocation) {
+        // a failed allocation is not sticky, but it stays the thread's "last error":
+        // clear it so that the next launch check does not report it again
+        (void)cudaGetLastError();
+        return GT_ERR_OOM;
+    }
     return GT_ERR_CUDA;
 }
 
@@ -97,6 +104,29 @@ gt_options effective(const gt_options &o)
     return e;
 }
 
+// The listing passes the spacetime parameters to its kernels as float32.
+void round_params_f32(CamDesc &d)
+{
+    d.M = (double)(float)d.M;
+    d.S = (double)(float)d.S;
+    d.Q = (double)(float)d.Q;
+}
+
+constexpr int PAPER_FLAGS = GT_FLAG_FD_DERIVS | GT_FLAG_F32_IO | GT_FLAG_EULER;
+
+// Kind hint of a launch: per camera with forward differences when asked for.
+int kind_for(int flags, int kind)
+{
+    return (flags & GT_FLAG_FD_DERIVS) ? (int)gt::KIND_FD : kind;
+}
+
+// Ring, redshift output and state arrays of a launch (all optional).
+struct Extra {
+    gt::DiskArgs disk = {};
+    double *z = nullptr;
+    gt::StateArrays states = {};
+};
+
 // Upload + set up the single camera if it changed; synchronous (reads validity).
 int prepare_camera(gt_ctx *c)
 {
@@ -104,6 +134,7 @@ int prepare_camera(gt_ctx *c)
     if (!c->cam_dirty && c->cam_flags == e.flags && c->cam_rsw == e.r_switch) return GT_OK;
     CamDesc d;
     fill_desc(d, c->M, c->S, c->Q, c->r0, c->th0, c->fov, c->res_x, c->res_y, 0);
+    if (e.flags & GT_FLAG_F32_IO) round_params_f32(d);
     cudaError_t err = cudaMemcpyAsync(c->d_cam, &d, sizeof d, cudaMemcpyHostToDevice, c->stream);
     if (err == cudaSuccess) err = gt::launch_camera_setup(c->d_cam, 1, e.flags, e.r_switch, c->stream);
     if (err == cudaSuccess)
@@ -309,10 +340,12 @@ int run_trace(gt_ctx *c, const CamDesc *d_cams, int n_cams, int kind_hint, int64
               int64_t n_rays, int64_t n_steps, double sp, int mode, double *t, double *r,
               double *th, double *ph, uint8_t *status, uint32_t *nsteps,
               const int64_t *fresh_ids = nullptr, const gt::RayParams *d_rays = nullptr,
-              bool compact_out = false)
+              bool compact_out = false, const Extra &x = Extra())
 {
     const gt_options e = effective(c->opts);
+    if ((e.flags & PAPER_FLAGS) && mode != GT_MODE_FP64) return GT_ERR_INVALID_ARG;
     if (n_rays == 0) return GT_OK;
+    kind_hint = kind_for(e.flags, kind_hint);
     gt::TraceArgs a;
     memset(&a, 0, sizeof a);
     a.cams = d_cams;
@@ -336,6 +369,11 @@ int run_trace(gt_ctx *c, const CamDesc *d_cams, int n_cams, int kind_hint, int64
     a.status = status;
     a.nsteps = nsteps;
     a.scratch = c->d_scratch;
+    a.euler = (e.flags & GT_FLAG_EULER) ? 1 : 0;
+    a.f32_io = (e.flags & GT_FLAG_F32_IO) ? 1 : 0;
+    a.disk = x.disk;
+    a.z = x.z;
+    a.states = x.states;
     cudaError_t err =
         cudaMemsetAsync(c->d_scratch, 0, gt::SCR_WORDS * sizeof(unsigned long long), c->stream);
     if (err != cudaSuccess) return cuda_code(err);
@@ -492,6 +530,7 @@ int gt_destroy(gt_ctx *c)
     cudaFree(c->d_park);
     cudaFree(c->d_rays);
     cudaFree(c->d_fallback);
+    cudaFree(c->d_state_cam);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
@@ -541,7 +580,7 @@ int gt_set_options(gt_ctx *c, const gt_options *o)
     if (!isfinite(v.r_switch) || !(v.timeout_seconds >= 0.0) || !isfinite(v.timeout_seconds))
         return GT_ERR_INVALID_ARG;
     if (v.flags & ~(GT_FLAG_COMPAT_WEIGHTS | GT_FLAG_COMPAT_CAMERA | GT_FLAG_ONE_SHOT |
-                    GT_FLAG_GRAPH | GT_FLAG_PRECISE_MN))
+                    GT_FLAG_GRAPH | GT_FLAG_PRECISE_MN | PAPER_FLAGS))
         return GT_ERR_INVALID_ARG;
     c->opts = v;
     return GT_OK;
@@ -595,6 +634,72 @@ int gt_trace_pixels(gt_ctx *c, const int64_t *pixels, int64_t n, int64_t n_steps
     const int kind = (c->Q != 0.0) ? gt::KIND_MN : gt::KIND_KERR;
     return run_trace(c, c->d_cam, 1, kind, 0, n, n_steps, sp, mode, t, r, th, ph, status, nsteps,
                      pixels, nullptr, true);
+}
+
+int gt_trace_disk(gt_ctx *c, double r_in, double r_out, double half_thickness, int64_t n_steps,
+                  double sp, int mode, double *t, double *r, double *th, double *ph,
+                  uint8_t *status, uint32_t *nsteps, double *z)
+{
+    int rc = check_common(c, n_steps, sp, mode);
+    if (rc != GT_OK) return rc;
+    if (!(r_in > 0.0) || !(r_out > r_in) || !isfinite(r_out) || !(half_thickness > 0.0) ||
+        !isfinite(half_thickness) || !z || !aligned8(z))
+        return GT_ERR_INVALID_ARG;
+    if (!c->st_set || !c->cam_set) return GT_ERR_NOT_CONFIGURED;
+    if (!aligned8(t) || !aligned8(r) || !aligned8(th) || !aligned8(ph) || ((uintptr_t)nsteps & 3u))
+        return GT_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    if (!g.ok) return GT_ERR_CUDA;
+    rc = prepare_camera(c);
+    if (rc != GT_OK) return rc;
+    if (!c->cam_valid) return GT_ERR_INVALID_ARG;
+    Extra x;
+    x.disk.on = 1;
+    x.disk.r_in = r_in;
+    x.disk.r_out = r_out;
+    x.disk.half_thickness = half_thickness;
+    x.z = z;
+    const int kind = (c->Q != 0.0) ? gt::KIND_MN : gt::KIND_KERR;
+    return run_trace(c, c->d_cam, 1, kind, 0, (int64_t)c->res_x * c->res_y, n_steps, sp, mode, t,
+                     r, th, ph, status, nsteps, nullptr, nullptr, false, x);
+}
+
+int gt_trace_states(gt_ctx *c, int64_t n, double *t, double *r, double *th, double *ph,
+                    double *pt, double *pr, double *pth, double *pph, double r_escape,
+                    int64_t n_steps, double sp, int mode, uint8_t *status, uint32_t *nsteps)
+{
+    int rc = check_common(c, n_steps, sp, mode);
+    if (rc != GT_OK) return rc;
+    if (n < 0 || !(r_escape > 0.0) || !isfinite(r_escape)) return GT_ERR_INVALID_ARG;
+    double *arr[8] = {t, r, th, ph, pt, pr, pth, pph};
+    for (double *p : arr)
+        if (!p || !aligned8(p)) return GT_ERR_INVALID_ARG;
+    if ((uintptr_t)nsteps & 3u) return GT_ERR_INVALID_ARG;
+    if (!c->st_set) return GT_ERR_NOT_CONFIGURED;
+    if (n == 0) return GT_OK;
+    DeviceGuard g(c->device);
+    if (!g.ok) return GT_ERR_CUDA;
+    const gt_options e = effective(c->opts);
+    cudaError_t err = cudaSuccess;
+    if (!c->d_state_cam) {
+        err = cudaMalloc(&c->d_state_cam, sizeof(CamDesc));
+        if (err != cudaSuccess) return cuda_code(err);
+    }
+    // the spacetime constants come from the camera set-up; the escape radius is
+    // 1.5 r0 there, so r0 = r_escape / 1.5 (the camera's own fields are not used)
+    CamDesc d;
+    fill_desc(d, c->M, c->S, c->Q, r_escape / 1.5, 0.5 * M_PI, 90.0, 1, 1, 0);
+    if (e.flags & GT_FLAG_F32_IO) round_params_f32(d);
+    err = cudaMemcpyAsync(c->d_state_cam, &d, sizeof d, cudaMemcpyHostToDevice, c->stream);
+    if (err == cudaSuccess)
+        err = gt::launch_camera_setup(c->d_state_cam, 1, e.flags, e.r_switch, c->stream);
+    if (err != cudaSuccess) return cuda_code(err);
+    Extra x;
+    x.states = {t, r, th, ph, pt, pr, pth, pph};
+    const int kind = (c->Q != 0.0) ? gt::KIND_MN : gt::KIND_KERR;
+    // the end states reach the arrays through x.states (positions included)
+    return run_trace(c, c->d_state_cam, 1, kind, 0, n, n_steps, sp, mode, nullptr, nullptr,
+                     nullptr, nullptr, status, nsteps, nullptr, nullptr, false, x);
 }
 
 int gt_trace_host(gt_ctx *c, int64_t n_steps, double sp, int mode, double *t, double *r,
@@ -656,6 +761,7 @@ int gt_trace_batch(gt_ctx *c, const gt_camera_desc *cams, int n_cams, int64_t n_
             !valid_camera(d.r0, d.theta0, d.fov_deg, d.res_x, d.res_y))
             return GT_ERR_INVALID_ARG;
         fill_desc(h[i], d.M, d.S, d.Q, d.r0, d.theta0, d.fov_deg, d.res_x, d.res_y, off);
+        if (c->opts.flags & GT_FLAG_F32_IO) round_params_f32(h[i]);
         off += (int64_t)d.res_x * d.res_y;
         if (d.Q != 0.0)
             any_mn = true;

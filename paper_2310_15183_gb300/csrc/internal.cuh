@@ -45,6 +45,11 @@ enum : int {
 // Kernel modes (public GT_MODE_FP32_MIXED runs MIXED_FP32 and ZONE_FP64 in rounds).
 enum : int { KMODE_FP64 = 0, KMODE_MIXED_INLINE = 1, KMODE_MIXED_FP32 = 2, KMODE_ZONE_FP64 = 3 };
 
+// Kind of a launch: one spacetime kind for every camera (KIND_KERR, KIND_MN), per camera
+// (KIND_ANY), or per camera with the listing's forward-difference metric derivatives
+// (KIND_FD, FP64 only).
+enum : int { KIND_ANY = 2, KIND_FD = 3 };
+
 // A ray handed between the FP32 and FP64-zone kernels (full state in FP64).
 struct ParkItem {
     int64_t id;
@@ -59,6 +64,18 @@ struct ParkItem {
 struct RayParams {
     const double *alpha, *beta, *spin, *q, *theta0; // device arrays; spin is a/M (S = spin M^2)
     double M, r0, r_switch;
+};
+
+// The ring of the paper's renders as an exit (Sec. 3.3.3): r_in <= r <= r_out and
+// |r cos theta| <= half_thickness; on = 0 disables it.
+struct DiskArgs {
+    int on;
+    double r_in, r_out, half_thickness;
+};
+
+// Ray states as inputs and outputs (gt_trace_states): SoA device arrays, updated in place.
+struct StateArrays {
+    double *t, *r, *th, *ph, *pt, *pr, *pth, *pph;
 };
 
 struct TraceArgs {
@@ -90,6 +107,13 @@ struct TraceArgs {
     uint8_t *status;
     uint32_t *nsteps;
     unsigned long long *scratch; // SCR_WORDS words
+    // paper-numerics and objects (FP64 kernels unless noted)
+    int euler;        // explicit Euler instead of RK4 (Sec. 3.1.1)
+    int f32_io;       // initial state and outputs rounded to float32 (listing)
+    DiskArgs disk;    // the ring exit (also in the FP32-mixed kernels)
+    double *z;        // redshift factor per ray (ring hits; NaN otherwise) or null
+    StateArrays states; // with states.t != null fresh rays start from these arrays and the
+                        // end states (all 8 components) are written back to them
 };
 
 // Host-side validation shared by every entry point that takes a spacetime or a camera

@@ -624,6 +624,39 @@ GT_HD void mn_rates_fwd(const SpacetimeT<T> &c, T r, T th, T pr, T pth, T pt, T 
     o.dpth = T(-0.5) * H2.t;
 }
 
+// (t, phi) block of the inverse metric, g^{tt}, g^{t phi}, g^{phi phi}, with N = D3<T>
+// (values and r, theta derivatives) or V1<T> (values): the ring emitter's circular orbit
+// needs their exact r derivatives.
+template <class T, class N>
+GT_HD void kerr_upper_tphi(const SpacetimeT<T> &c, T r, T th, N g[3])
+{
+    T s, cs;
+    sincos_t(th, &s, &cs);
+    const T a = T(c.a), a2 = T(c.a2), M = T(c.M);
+    N R, S2, C2;
+    mkvar(R, r, T(1), T(0));
+    mkvar(S2, s * s, T(0), T(2) * s * cs);
+    mkvar(C2, cs * cs, T(0), T(-2) * s * cs);
+    const N r2 = dsq(R);
+    const N ra2 = r2 + a2;
+    const N Sigma = r2 + C2 * a2;
+    const N Delta = r2 - R * (T(2) * M) + a2;
+    const N iD = drcp(Sigma * Delta);
+    g[0] = -(dsq(ra2) - Delta * S2 * a2) * iD;
+    g[1] = R * iD * (T(-2) * M * a);
+    g[2] = (Delta - S2 * a2) * iD * drcp(S2);
+}
+
+template <class T, class N>
+GT_HD void mn_upper_tphi(const SpacetimeT<T> &c, T r, T th, N g[3])
+{
+    MNPot<N> P;
+    mn_potentials<T, N>(c, r, th, P);
+    g[0] = -P.invf + dsq(P.om) * P.F;
+    g[1] = P.om * P.F;
+    g[2] = P.F;
+}
+
 #ifdef __CUDACC__
 __device__ __forceinline__ void mn_upper(const SpacetimeC &c, double r, double th, double g[5])
 {

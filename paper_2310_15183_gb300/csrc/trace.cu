@@ -126,34 +126,81 @@ __device__ __forceinline__ void rates_any(const SpacetimeC &st, double r, double
                                           double pr, double pth, double pt, double pph,
                                           Rates<double> &o)
 {
-    if (KIND == KIND_KERR || (KIND == 2 && st.kind == KIND_KERR))
+    if (KIND == KIND_KERR || (KIND == KIND_ANY && st.kind == KIND_KERR))
         kerr_rates_sc<double>(st, r, s, cs, pr, pth, pt, pph, o);
     else
         mn_rates_sc<double>(st, r, s, cs, pr, pth, pt, pph, o);
 }
 
+// The listing's numerics (KIND_FD): the inverse metric at (r, theta) and the forward
+// differences d_r g ~ (g(r + delta, theta) - g(r, theta))/delta, d_theta likewise, with
+// delta = derPrecision = 1e-8 -- three metric evaluations -- contracted into
+// dp = -1/2 d g^{nu sigma} p_nu p_sigma component by component.
+constexpr double FD_DELTA = 1e-8;
+
+__device__ __forceinline__ double fd_quad(const double d[5], double pr, double pth, double pt,
+                                          double pph)
+{
+    return d[0] * pt * pt + 2.0 * d[1] * pt * pph + d[2] * pph * pph + d[3] * pr * pr +
+           d[4] * pth * pth;
+}
+
+__device__ __forceinline__ void rates_fd(const SpacetimeC &st, double r, double th, double pr,
+                                         double pth, double pt, double pph, Rates<double> &o)
+{
+    double g0[5], gr[5], gt[5], dr[5], dt[5];
+    upper_metric(st, r, th, g0);
+    upper_metric(st, r + FD_DELTA, th, gr);
+    upper_metric(st, r, th + FD_DELTA, gt);
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        dr[i] = (gr[i] - g0[i]) / FD_DELTA;
+        dt[i] = (gt[i] - g0[i]) / FD_DELTA;
+    }
+    o.dt = g0[0] * pt + g0[1] * pph;
+    o.dph = g0[1] * pt + g0[2] * pph;
+    o.dr = g0[3] * pr;
+    o.dth = g0[4] * pth;
+    o.dpr = -0.5 * fd_quad(dr, pr, pth, pt, pph);
+    o.dpth = -0.5 * fd_quad(dt, pr, pth, pt, pph);
+}
+
 // One FP64 RK4 step; returns h and writes the candidate state to y.  sin and cos of
 // theta are evaluated once per step and rotated to the later stages by their small
-// angle offsets (Taylor series, FP64 accurate).
+// angle offsets (Taylor series, FP64 accurate); the forward-difference kind evaluates
+// its metric at each stage's theta as the listing does.
 template <int KIND>
 __device__ __forceinline__ double rk4_step64(const SpacetimeC &st, const Ray64 &x, double sp,
                                              double w6, Ray64 &y)
 {
     Rates<double> k1, k2, k3, k4;
-    double s1, c1, s, c;
-    sincos(x.th, &s1, &c1);
-    rates_any<KIND>(st, x.r, s1, c1, x.pr, x.pth, x.pt, x.pph, k1);
-    const double h = fabs(sp / k1.dt);
-    const double hh = 0.5 * h;
-    rotate_sc(s1, c1, x.th, hh * k1.dth, &s, &c);
-    rates_any<KIND>(st, x.r + hh * k1.dr, s, c, x.pr + hh * k1.dpr, x.pth + hh * k1.dpth, x.pt,
-                    x.pph, k2);
-    rotate_sc(s1, c1, x.th, hh * k2.dth, &s, &c);
-    rates_any<KIND>(st, x.r + hh * k2.dr, s, c, x.pr + hh * k2.dpr, x.pth + hh * k2.dpth, x.pt,
-                    x.pph, k3);
-    rotate_sc(s1, c1, x.th, h * k3.dth, &s, &c);
-    rates_any<KIND>(st, x.r + h * k3.dr, s, c, x.pr + h * k3.dpr, x.pth + h * k3.dpth, x.pt,
-                    x.pph, k4);
+    double h, hh;
+    if constexpr (KIND == KIND_FD) {
+        rates_fd(st, x.r, x.th, x.pr, x.pth, x.pt, x.pph, k1);
+        h = fabs(sp / k1.dt);
+        hh = 0.5 * h;
+        rates_fd(st, x.r + hh * k1.dr, x.th + hh * k1.dth, x.pr + hh * k1.dpr,
+                 x.pth + hh * k1.dpth, x.pt, x.pph, k2);
+        rates_fd(st, x.r + hh * k2.dr, x.th + hh * k2.dth, x.pr + hh * k2.dpr,
+                 x.pth + hh * k2.dpth, x.pt, x.pph, k3);
+        rates_fd(st, x.r + h * k3.dr, x.th + h * k3.dth, x.pr + h * k3.dpr,
+                 x.pth + h * k3.dpth, x.pt, x.pph, k4);
+    } else {
+        double s1, c1, s, c;
+        sincos(x.th, &s1, &c1);
+        rates_any<KIND>(st, x.r, s1, c1, x.pr, x.pth, x.pt, x.pph, k1);
+        h = fabs(sp / k1.dt);
+        hh = 0.5 * h;
+        rotate_sc(s1, c1, x.th, hh * k1.dth, &s, &c);
+        rates_any<KIND>(st, x.r + hh * k1.dr, s, c, x.pr + hh * k1.dpr, x.pth + hh * k1.dpth,
+                        x.pt, x.pph, k2);
+        rotate_sc(s1, c1, x.th, hh * k2.dth, &s, &c);
+        rates_any<KIND>(st, x.r + hh * k2.dr, s, c, x.pr + hh * k2.dpr, x.pth + hh * k2.dpth,
+                        x.pt, x.pph, k3);
+        rotate_sc(s1, c1, x.th, h * k3.dth, &s, &c);
+        rates_any<KIND>(st, x.r + h * k3.dr, s, c, x.pr + h * k3.dpr, x.pth + h * k3.dpth, x.pt,
+                        x.pph, k4);
+    }
     const double hw = h * w6;
     y.t = x.t + hw * (k1.dt + 2.0 * k2.dt + 2.0 * k3.dt + k4.dt);
     y.r = x.r + hw * (k1.dr + 2.0 * k2.dr + 2.0 * k3.dr + k4.dr);
@@ -166,21 +213,142 @@ __device__ __forceinline__ double rk4_step64(const SpacetimeC &st, const Ray64 &
     return h;
 }
 
+// One explicit Euler step (Sec. 3.1.1): x += h F(x) with the same step rule.
+template <int KIND>
+__device__ __forceinline__ double euler_step64(const SpacetimeC &st, const Ray64 &x, double sp,
+                                               Ray64 &y)
+{
+    Rates<double> k1;
+    if constexpr (KIND == KIND_FD) {
+        rates_fd(st, x.r, x.th, x.pr, x.pth, x.pt, x.pph, k1);
+    } else {
+        double s1, c1;
+        sincos(x.th, &s1, &c1);
+        rates_any<KIND>(st, x.r, s1, c1, x.pr, x.pth, x.pt, x.pph, k1);
+    }
+    const double h = fabs(sp / k1.dt);
+    y.t = x.t + h * k1.dt;
+    y.r = x.r + h * k1.dr;
+    y.th = x.th + h * k1.dth;
+    y.ph = x.ph + h * k1.dph;
+    y.pr = x.pr + h * k1.dpr;
+    y.pth = x.pth + h * k1.dpth;
+    y.pt = x.pt;
+    y.pph = x.pph;
+    return h;
+}
+
+template <int KIND>
+__device__ __forceinline__ double step64(const TraceArgs &A, const SpacetimeC &st, const Ray64 &x,
+                                         Ray64 &y)
+{
+    if (A.euler) return euler_step64<KIND>(st, x, A.sp, y);
+    return rk4_step64<KIND>(st, x, A.sp, A.w6, y);
+}
+
+// ------------------------------------------------------------------ ring and redshift
+__device__ __forceinline__ bool in_disk(const DiskArgs &dk, double r, double th)
+{
+    return r >= dk.r_in && r <= dk.r_out && fabs(r * cos(th)) <= dk.half_thickness;
+}
+
+// Redshift factor of the ray x at the ring (Sec. 3.3.3): the emitter moves on the
+// circular orbit through (r, theta) -- p_r = p_theta = 0, dp_r/dtau = 0 and p_t = -1,
+// i.e. A p_phi^2 - 2 B p_phi + C = 0 with (A, B, C) = d_r (g^{phi phi}, g^{t phi}, g^{tt}),
+// the root with positive angular velocity, rescaled to g^{mu nu} p_mu p_nu = -1 -- and
+// z = (p . u_S) / (p . u_O), u_O the static observer at the camera, p . u_O =
+// p_t / sqrt(-g_tt(camera)).  Exact r derivatives by dual numbers (forward differences
+// with KIND_FD).  NaN where no timelike circular orbit exists.
+template <int KIND>
+__device__ double redshift64(const SpacetimeC &st, double gl_tt_cam, const Ray64 &x)
+{
+    double g[3], A, B, C;
+    if (KIND == KIND_FD) {
+        double g0[5], gr[5];
+        upper_metric(st, x.r, x.th, g0);
+        upper_metric(st, x.r + FD_DELTA, x.th, gr);
+        A = (gr[2] - g0[2]) / FD_DELTA;
+        B = (gr[1] - g0[1]) / FD_DELTA;
+        C = (gr[0] - g0[0]) / FD_DELTA;
+        g[0] = g0[0];
+        g[1] = g0[1];
+        g[2] = g0[2];
+    } else {
+        D3<double> gd[3];
+        if (st.kind == KIND_KERR)
+            kerr_upper_tphi<double, D3<double>>(st, x.r, x.th, gd);
+        else
+            mn_upper_tphi<double, D3<double>>(st, x.r, x.th, gd);
+        C = gd[0].r;
+        B = gd[1].r;
+        A = gd[2].r;
+        g[0] = gd[0].v;
+        g[1] = gd[1].v;
+        g[2] = gd[2].v;
+    }
+    const double disc = B * B - A * C;
+    if (!(disc >= 0.0) || A == 0.0) return nan("");
+    const double sq = sqrt(disc);
+    const double roots[2] = {(B + sq) / A, (B - sq) / A};
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const double pph = roots[k];
+        const double ut = -g[0] + g[1] * pph;
+        const double uph = -g[1] + g[2] * pph;
+        const double norm = g[0] - 2.0 * g[1] * pph + g[2] * pph * pph;
+        if (ut > 0.0 && uph / ut > 0.0 && norm < 0.0) {
+            const double lam = 1.0 / sqrt(-norm);
+            const double num = (x.pt * ut + x.pph * uph) * lam;
+            return num / (x.pt / sqrt(-gl_tt_cam));
+        }
+    }
+    return nan("");
+}
+
 __device__ __forceinline__ bool finite6(const Ray64 &y)
 {
     return isfinite(y.t) && isfinite(y.r) && isfinite(y.th) && isfinite(y.ph) && isfinite(y.pr) &&
            isfinite(y.pth);
 }
 
+__device__ __forceinline__ double round_f32(double v) { return (double)(float)v; }
+
+// End position of a ray that did not run (watchdog drain): position outputs only.
 __device__ __forceinline__ void store_ray(const TraceArgs &A, int64_t id, double t, double r,
                                           double th, double ph, int status, uint32_t n)
 {
+    if (A.f32_io) {
+        t = round_f32(t);
+        r = round_f32(r);
+        th = round_f32(th);
+        ph = round_f32(ph);
+    }
     if (A.t) A.t[id] = t;
     if (A.r) A.r[id] = r;
     if (A.th) A.th[id] = th;
     if (A.ph) A.ph[id] = ph;
     if (A.status) A.status[id] = (uint8_t)status;
     if (A.nsteps) A.nsteps[id] = n;
+    if (A.z) A.z[id] = nan("");
+}
+
+// End state of a ray: position outputs (float32-rounded with f32_io), the redshift
+// factor, and with state arrays the whole state written back.
+__device__ __forceinline__ void store_full(const TraceArgs &A, int64_t id, const Ray64 &x,
+                                           int status, uint32_t n, double z)
+{
+    store_ray(A, id, x.t, x.r, x.th, x.ph, status, n);
+    if (A.z) A.z[id] = z;
+    if (A.states.t) {
+        A.states.t[id] = x.t;
+        A.states.r[id] = x.r;
+        A.states.th[id] = x.th;
+        A.states.ph[id] = x.ph;
+        A.states.pt[id] = x.pt;
+        A.states.pr[id] = x.pr;
+        A.states.pth[id] = x.pth;
+        A.states.pph[id] = x.pph;
+    }
 }
 
 // Camera of flat ray id (binary search over the prefix offsets).
@@ -315,7 +483,8 @@ __device__ __forceinline__ void reproject_pr(const SpacetimeC &st, Ray64 &x)
 //         parked on the output list; input list items continue in FP32.
 // MODE 3: FP64 zone steps for parked rays; a ray leaving the zone (r > 1.25 r_switch)
 //         is parked on the output list for the next FP32 launch.
-// KIND: 0 Kerr, 1 Manko-Novikov, 2 per-camera.
+// KIND: 0 Kerr, 1 Manko-Novikov, 2 per-camera, 3 per-camera with forward-difference
+// derivatives (MODE 0 only).
 // Work of a launch: fresh rays [0, n_fresh) then input-list items [0, *in_count).
 
 __device__ __forceinline__ void park(const TraceArgs &A, int64_t id, uint32_t n, int cam,
@@ -419,12 +588,36 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A, int one_shot)
                     store_ray(A, id, x.t, x.r, x.th, x.ph, valid ? GT_RAY_MAXSTEPS : GT_RAY_NONFINITE, 0);
                     return false;
                 }
-            } else {
-                if (KIND == 2 || A.n_cams > 1) load_camera(find_camera(cams, A.n_cams, pix));
-                camera_init(cams[cam], A.first + pix - cams[cam].offset, x);
+            } else if (A.states.t) { // an arbitrary initial state (gt_trace_states)
+                x.t = A.states.t[pix];
+                x.r = A.states.r[pix];
+                x.th = A.states.th[pix];
+                x.ph = A.states.ph[pix];
+                x.pt = A.states.pt[pix];
+                x.pr = A.states.pr[pix];
+                x.pth = A.states.pth[pix];
+                x.pph = A.states.pph[pix];
                 n = 0;
                 if (A.n_steps <= 0) {
-                    store_ray(A, id, x.t, x.r, x.th, x.ph, GT_RAY_MAXSTEPS, 0);
+                    store_full(A, id, x, GT_RAY_MAXSTEPS, 0, nan(""));
+                    return false;
+                }
+            } else {
+                if (KIND >= KIND_ANY || A.n_cams > 1) load_camera(find_camera(cams, A.n_cams, pix));
+                camera_init(cams[cam], A.first + pix - cams[cam].offset, x);
+                if (A.f32_io) { // the listing's kernels take the initial state as float32
+                    x.t = round_f32(x.t);
+                    x.r = round_f32(x.r);
+                    x.th = round_f32(x.th);
+                    x.ph = round_f32(x.ph);
+                    x.pt = round_f32(x.pt);
+                    x.pr = round_f32(x.pr);
+                    x.pth = round_f32(x.pth);
+                    x.pph = round_f32(x.pph);
+                }
+                n = 0;
+                if (A.n_steps <= 0) {
+                    store_full(A, id, x, GT_RAY_MAXSTEPS, 0, nan(""));
                     return false;
                 }
             }
@@ -434,7 +627,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A, int one_shot)
             n = it.n;
             if (A.rays)
                 load_rayparams(id, false);
-            else if (KIND == 2 || A.n_cams > 1)
+            else if (KIND >= KIND_ANY || A.n_cams > 1)
                 load_camera(it.cam);
             x.t = it.t;
             x.r = it.r;
@@ -498,7 +691,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A, int one_shot)
             if (stop) {
                 if (active) {
                     if (MODE == 1 || MODE == 2) mixed_to64(m, x);
-                    store_ray(A, id, x.t, x.r, x.th, x.ph, GT_RAY_TIMEOUT, n);
+                    store_full(A, id, x, GT_RAY_TIMEOUT, n, nan(""));
                 }
                 if (!one_shot) {
                     for (;;) { // drain the queue without integrating
@@ -508,7 +701,10 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A, int one_shot)
                         if (base >= (unsigned long long)n_work) break;
                         const int64_t w = (int64_t)base + lane;
                         if (w < n_work) {
-                            if (w < A.n_fresh) {
+                            if (w < A.n_fresh && A.states.t) {
+                                if (A.status) A.status[w] = GT_RAY_TIMEOUT; // state untouched
+                                if (A.nsteps) A.nsteps[w] = 0;
+                            } else if (w < A.n_fresh) {
                                 const int64_t pix = A.fresh_ids ? A.fresh_ids[w] : w;
                                 const int c = A.n_cams > 1 ? find_camera(cams, A.n_cams, pix) : 0;
                                 const double r0 = A.rays ? A.rays->r0 : cams[c].r0;
@@ -517,7 +713,16 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A, int one_shot)
                                           th0, 0.0, GT_RAY_TIMEOUT, 0);
                             } else {
                                 const ParkItem &p = A.in_items[w - A.n_fresh];
-                                store_ray(A, p.id, p.t, p.r, p.th, p.ph, GT_RAY_TIMEOUT, p.n);
+                                Ray64 y;
+                                y.t = p.t;
+                                y.r = p.r;
+                                y.th = p.th;
+                                y.ph = p.ph;
+                                y.pt = p.pt;
+                                y.pr = p.pr;
+                                y.pth = p.pth;
+                                y.pph = p.pph;
+                                store_full(A, p.id, y, GT_RAY_TIMEOUT, p.n, nan(""));
                             }
                         }
                     }
@@ -531,13 +736,16 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A, int one_shot)
         int status = -1;
         if (MODE == 0 || MODE == 3) {
             Ray64 y;
-            const double h = rk4_step64<KIND>(st, x, A.sp, A.w6, y);
+            const double h = step64<KIND>(A, st, x, y);
             ++n;
             if (!isfinite(h) || !finite6(y)) {
                 status = GT_RAY_NONFINITE;
             } else {
                 x = y;
                 status = exit_status(x.r, h, r_esc, A.sp, n, A.n_steps);
+                // the ring is tested after the escape and before the horizon
+                if (A.disk.on && status != GT_RAY_ESCAPED && in_disk(A.disk, x.r, x.th))
+                    status = GT_RAY_DISK;
                 if (MODE == 3 && status < 0 && x.r > 1.25 * r_sw) { // leave the FP64 zone
                     bool ok;
                     park(A, id, n, cam, x, &ok);
@@ -550,7 +758,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A, int one_shot)
             if ((double)m.r.hi < r_sw) { // FP64 zone inline
                 Ray64 y;
                 mixed_to64(m, x);
-                h = rk4_step64<KIND>(st, x, A.sp, A.w6, y);
+                h = step64<KIND>(A, st, x, y);
                 ok = isfinite(h) && finite6(y);
                 if (ok) mixed_from64(y, m);
             } else {
@@ -567,6 +775,8 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A, int one_shot)
             } else {
                 const double r_now = f2_to(m.r);
                 status = exit_status(r_now, h, r_esc, A.sp, n, A.n_steps);
+                if (A.disk.on && status != GT_RAY_ESCAPED && in_disk(A.disk, r_now, f2_to(m.th)))
+                    status = GT_RAY_DISK;
                 if (status >= 0) {
                     mixed_to64(m, x);
                 } else if (n == rp_next) {
@@ -590,6 +800,8 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A, int one_shot)
                 status = GT_RAY_NONFINITE;
             } else if (m.r.hi > r_esc_f.hi || (m.r.hi == r_esc_f.hi && m.r.lo > r_esc_f.lo)) {
                 status = GT_RAY_ESCAPED;
+            } else if (A.disk.on && in_disk(A.disk, f2_to(m.r), f2_to(m.th))) {
+                status = GT_RAY_DISK;
             } else if (h < h_thr_f) {
                 status = GT_RAY_HORIZON;
             } else if ((int64_t)n >= A.n_steps) {
@@ -626,7 +838,9 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A, int one_shot)
             if (status >= 0) mixed_to64(m, x);
         }
         if (status >= 0) {
-            store_ray(A, id, x.t, x.r, x.th, x.ph, status, n);
+            double z = nan("");
+            if (status == GT_RAY_DISK && A.z) z = redshift64<KIND>(cams[cam].st, cams[cam].gl_tt, x);
+            store_full(A, id, x, status, n, z);
             active = false;
         }
     }
@@ -673,7 +887,11 @@ static cudaError_t launch_mode(const TraceArgs &a, int kind_hint, int block, int
 {
     if (kind_hint == KIND_KERR) return launch_one<MODE, KIND_KERR>(a, block, grid, one_shot, s);
     if (kind_hint == KIND_MN) return launch_one<MODE, KIND_MN>(a, block, grid, one_shot, s);
-    return launch_one<MODE, 2>(a, block, grid, one_shot, s);
+    if (kind_hint == KIND_FD) {
+        if constexpr (MODE == 0) return launch_one<0, KIND_FD>(a, block, grid, one_shot, s);
+        return cudaErrorInvalidValue; // the listing's numerics run in FP64 only
+    }
+    return launch_one<MODE, KIND_ANY>(a, block, grid, one_shot, s);
 }
 
 cudaError_t launch_trace(const TraceArgs &args, int kmode, int kind_hint, int block, int grid,
@@ -707,7 +925,11 @@ static int occupancy_mode(int kind_hint, int block)
 {
     if (kind_hint == KIND_KERR) return occupancy_one<MODE, KIND_KERR>(block);
     if (kind_hint == KIND_MN) return occupancy_one<MODE, KIND_MN>(block);
-    return occupancy_one<MODE, 2>(block);
+    if (kind_hint == KIND_FD) {
+        if constexpr (MODE == 0) return occupancy_one<0, KIND_FD>(block);
+        return 1;
+    }
+    return occupancy_one<MODE, KIND_ANY>(block);
 }
 
 int max_blocks_per_sm(int kmode, int kind_hint, int block)

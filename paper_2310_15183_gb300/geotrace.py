@@ -19,9 +19,12 @@ LIB_PATH = os.path.join(_HERE, "libgeotrace.so")
 GT_OK = 0
 ERRORS = {-1: "invalid argument", -2: "not configured", -3: "CUDA error", -4: "out of memory",
           -5: "device watchdog timeout", -6: "unsupported device or feature"}
-ESCAPED, HORIZON, MAXSTEPS, NONFINITE, TIMEOUT = 0, 1, 2, 3, 4
+ESCAPED, HORIZON, MAXSTEPS, NONFINITE, TIMEOUT, DISK = 0, 1, 2, 3, 4, 5
 MODE_FP64, MODE_FP32_MIXED = 0, 1
 FLAG_COMPAT_WEIGHTS, FLAG_COMPAT_CAMERA, FLAG_ONE_SHOT, FLAG_GRAPH, FLAG_PRECISE_MN = 1, 2, 4, 8, 16
+FLAG_FD_DERIVS, FLAG_F32_IO, FLAG_EULER = 32, 64, 128
+# the listing's numerics: forward differences, float32 I/O, 0.1667 weights, v^phi = alpha
+FLAGS_PAPER = FLAG_FD_DERIVS | FLAG_F32_IO | FLAG_COMPAT_WEIGHTS | FLAG_COMPAT_CAMERA
 
 # every symbol include/geotrace.h declares
 EXPORTS = ("gt_create", "gt_destroy", "gt_set_stream", "gt_set_spacetime", "gt_set_camera",
@@ -30,7 +33,7 @@ EXPORTS = ("gt_create", "gt_destroy", "gt_set_stream", "gt_set_spacetime", "gt_s
            "gt_trace_rays", "gt_autotune", "gt_surrogate_num_params", "gt_surrogate_create",
            "gt_surrogate_destroy", "gt_surrogate_get_params", "gt_surrogate_set_params",
            "gt_surrogate_eval", "gt_surrogate_grad", "gt_surrogate_train", "gt_surrogate_infer",
-           "gt_strerror")
+           "gt_trace_disk", "gt_trace_states", "gt_strerror")
 
 
 class GeotraceError(RuntimeError):
@@ -87,6 +90,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.gt_trace_range.argtypes = [vp, i64, i64, i64, d, i] + out6
     lib.gt_trace_pixels.argtypes = [vp, vp, i64, i64, d, i] + out6
     lib.gt_trace_host.argtypes = [vp, i64, d, i] + out6
+    lib.gt_trace_disk.argtypes = [vp, d, d, d, i64, d, i] + out6 + [vp]
+    lib.gt_trace_states.argtypes = [vp, i64] + [vp] * 8 + [d, i64, d, i, vp, vp]
     lib.gt_trace_batch.argtypes = [vp, ctypes.POINTER(CameraDesc), i, i64, d, i] + out6
     lib.gt_sync.argtypes = [vp]
     lib.gt_device_sm_count.argtypes = [vp, ctypes.POINTER(i)]
@@ -227,6 +232,40 @@ class Tracer:
                                       *[_ptr(out.get(k)) for k in ("t", "r", "th", "ph",
                                                                     "status", "nsteps")])
         _check(rc, "gt_trace_pixels")
+        return out
+
+    def trace_disk(self, r_in: float, r_out: float, half_thickness: float, n_steps: int,
+                   step_precision: float, mode: int = MODE_FP64,
+                   out: Optional[dict] = None) -> dict:
+        """gt_trace_disk: the camera with the ring as an exit; adds "z" (redshift factor)."""
+        n = self.res[0] * self.res[1]
+        if out is None:
+            out = self.alloc_outputs(n)
+            out["z"] = self._torch.empty(n, dtype=self._torch.float64,
+                                         device=out["t"].device)
+        rc = self.lib.gt_trace_disk(self.ctx, float(r_in), float(r_out), float(half_thickness),
+                                    int(n_steps), float(step_precision), int(mode),
+                                    *[_ptr(out.get(k)) for k in ("t", "r", "th", "ph", "status",
+                                                                  "nsteps", "z")])
+        _check(rc, "gt_trace_disk")
+        return out
+
+    def trace_states(self, states: dict, r_escape: float, n_steps: int, step_precision: float,
+                     mode: int = MODE_FP64, out: Optional[dict] = None) -> dict:
+        """gt_trace_states: integrate the float64 device tensors states["t", "r", "th",
+        "ph", "pt", "pr", "pth", "pph"] in place; returns status and nsteps of this call."""
+        torch = self._torch
+        n = states["t"].numel()
+        if out is None:
+            dev = states["t"].device
+            out = {"status": torch.empty(n, dtype=torch.uint8, device=dev),
+                   "nsteps": torch.empty(n, dtype=torch.int32, device=dev)}
+        rc = self.lib.gt_trace_states(self.ctx, n, *[_ptr(states[k]) for k in
+                                                     ("t", "r", "th", "ph", "pt", "pr", "pth",
+                                                      "pph")],
+                                      float(r_escape), int(n_steps), float(step_precision),
+                                      int(mode), _ptr(out["status"]), _ptr(out["nsteps"]))
+        _check(rc, "gt_trace_states")
         return out
 
     def trace_host(self, n_steps: int, step_precision: float, mode: int = MODE_FP64,

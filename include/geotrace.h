@@ -273,22 +273,36 @@ int gt_surrogate_train(gt_ctx *ctx, gt_surrogate *s, const gt_train_cfg *cfg, in
                        const double *q, const double *theta0, const uint8_t *status,
                        const double *th_end, const double *ph_end, float *loss_per_epoch);
 
-/* Image of the configured camera through the surrogate: pixels with |logit| >= tau that
- * are not in the photon-ring band (Kerr: |min_r R(r)/(E^2 r^4)| < band from the pixel's
- * constants of motion; band = 0 disables) and, when predicted to escape, whose predicted
- * direction vector has a length within dir_tol of 1 (dir_tol = 0 disables; the network
- * is trained on unit vectors, and a shorter or longer one marks a region where it has not
- * settled) take the network's answer -- status ESCAPED with end theta, phi from the
- * predicted direction, or HORIZON with NaN angles; t and r are NaN and nsteps 0 for
- * them.  All other pixels are traced by the integrator (mode, n_steps, step_precision as
- * gt_trace) and written in place.  Outputs as gt_trace (device, res_x*res_y each, none
- * may be NULL); *n_fallback receives the number of integrated pixels.  Errors:
- * GT_ERR_INVALID_ARG (negative tau, band or dir_tol, NULL pointers) and those of
- * gt_trace.  Synchronous. */
+/* Image of the configured camera through the surrogate, with the integrator as judge and
+ * fallback.  With probe_stride > 0 the integrator first traces the probe pixels
+ * (i, j) with i, j multiples of probe_stride or the last column/row (images of at least
+ * 2 x 2 pixels); their exact results go to the image, and each probe records the
+ * network's error vector (exact unit end direction minus the predicted one).  A pixel
+ * inside a probe cell is then taken from the network only when the cell's four corners
+ * are classified alike by the integrator and the network -- all escaped, or all HORIZON
+ * -- and, when escaping, the corners' error vectors differ by less than probe_tol
+ * (|e00 - e11| and |e01 - e10|); its end direction is the network's plus the bilinear
+ * interpolation of the corner errors.  In every case a pixel also needs |logit| >= tau,
+ * lies outside the Kerr photon-ring band (|min_r R(r)/(E^2 r^4)| < band over 97
+ * geometric radii from 1.0001 r_+ to r0, from the pixel's constants of motion;
+ * band = 0 disables) and, when predicted to escape, has a predicted direction vector of
+ * length within dir_tol of 1 (dir_tol = 0 disables).  Network pixels get status
+ * ESCAPED with end theta, phi from the (corrected) direction, or HORIZON with NaN
+ * angles; t and r are NaN and nsteps 0 for them.  All other pixels are traced by the
+ * integrator (mode, n_steps, step_precision as gt_trace) and written in place.  Outputs
+ * as gt_trace (device, res_x*res_y each, none may be NULL); *n_fallback receives the
+ * number of integrated pixels besides the probes, *n_probes the number of probes (either
+ * may be NULL).  Errors: GT_ERR_INVALID_ARG (negative tau, band, dir_tol, probe_stride or
+ * probe_tol, NULL outputs) and those of gt_trace.  Synchronous. */
 int gt_surrogate_infer(gt_ctx *ctx, gt_surrogate *s, float tau, double band, float dir_tol,
-                       int64_t n_steps, double step_precision, int mode, double *t, double *r,
-                       double *theta, double *phi, uint8_t *status, uint32_t *nsteps,
-                       int64_t *n_fallback);
+                       int probe_stride, float probe_tol, int64_t n_steps,
+                       double step_precision, int mode, double *t, double *r, double *theta,
+                       double *phi, uint8_t *status, uint32_t *nsteps, int64_t *n_fallback,
+                       int64_t *n_probes);
+
+/* Copy the float32 gradient of the last training step (or of gt_surrogate_grad) to a host
+ * array of gt_surrogate_num_params floats. */
+int gt_surrogate_get_grads(gt_surrogate *s, float *host, int64_t n);
 
 /* Largest batch gt_trace_batch_noalloc accepts. */
 #define GT_NOALLOC_MAX_CAMS 64

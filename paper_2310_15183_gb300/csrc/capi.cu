@@ -11,6 +11,7 @@
 
 #include "../../include/geotrace.h"
 #include "internal.cuh"
+#include "surrogate.cuh"
 
 using gt::CamDesc;
 using gt::fill_desc;
@@ -53,6 +54,9 @@ struct gt_ctx {
     gt::RayParams *d_rays = nullptr;
     // spacetime descriptor of gt_trace_states (no camera)
     CamDesc *d_state_cam = nullptr;
+    // integrator probes of gated surrogate inference: pixel list, exact results, records
+    void *d_probe = nullptr;
+    int64_t probe_cap = 0;
     int64_t *d_fallback = nullptr;
     int64_t fallback_cap = 0;
 };
@@ -62,9 +66,15 @@ cudaStream_t gt_internal_stream(gt_ctx *c) { return c->stream; }
 namespace gt {
 namespace sg {
 int infer_chunks(gt_surrogate *s, const CamDesc *d_cam, int64_t n_pix, float tau, double band,
-                 float dir_tol, double *t, double *r, double *th, double *ph, uint8_t *status,
-                 uint32_t *nsteps, int64_t *d_fallback, unsigned long long *d_nfb, cudaStream_t st);
-}
+                 float dir_tol, const ProbeGrid &pg, double *t, double *r, double *th, double *ph,
+                 uint8_t *status, uint32_t *nsteps, int64_t *d_fallback, unsigned long long *d_nfb,
+                 cudaStream_t st);
+int probe_pixels(const CamDesc *d_cam, const ProbeGrid &pg, int64_t *d_pix, cudaStream_t st);
+int probe_records(gt_surrogate *s, const CamDesc *d_cam, const int64_t *d_pix, int n,
+                  const double *pt, const double *pr, const double *pth, const double *pph,
+                  const uint8_t *pst, const uint32_t *pns, ProbeRec *rec, double *t, double *r,
+                  double *th, double *ph, uint8_t *status, uint32_t *nsteps, cudaStream_t st);
+} // namespace sg
 } // namespace gt
 
 namespace {
@@ -531,6 +541,7 @@ int gt_destroy(gt_ctx *c)
     cudaFree(c->d_rays);
     cudaFree(c->d_fallback);
     cudaFree(c->d_state_cam);
+    cudaFree(c->d_probe);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
@@ -832,13 +843,14 @@ int gt_trace_rays(gt_ctx *c, int64_t n, const double *alpha, const double *beta,
 }
 
 int gt_surrogate_infer(gt_ctx *c, gt_surrogate *s, float tau, double band, float dir_tol,
-                       int64_t n_steps, double sp, int mode, double *t, double *r, double *th,
-                       double *ph, uint8_t *status, uint32_t *nsteps, int64_t *n_fallback)
+                       int probe_stride, float probe_tol, int64_t n_steps, double sp, int mode,
+                       double *t, double *r, double *th, double *ph, uint8_t *status,
+                       uint32_t *nsteps, int64_t *n_fallback, int64_t *n_probes)
 {
     int rc = check_common(c, n_steps, sp, mode);
     if (rc != GT_OK) return rc;
     if (!s || !t || !r || !th || !ph || !status || !nsteps || !(tau >= 0.0f) || !(band >= 0.0) ||
-        !(dir_tol >= 0.0f))
+        !(dir_tol >= 0.0f) || probe_stride < 0 || !(probe_tol >= 0.0f))
         return GT_ERR_INVALID_ARG;
     if (!c->st_set || !c->cam_set) return GT_ERR_NOT_CONFIGURED;
     if (!aligned8(t) || !aligned8(r) || !aligned8(th) || !aligned8(ph) || ((uintptr_t)nsteps & 3u))
@@ -858,10 +870,47 @@ int gt_surrogate_infer(gt_ctx *c, gt_surrogate *s, float tau, double band, float
         if (e != cudaSuccess) return cuda_code(e);
         c->fallback_cap = n_pix;
     }
+    const int kind = (c->Q != 0.0) ? gt::KIND_MN : gt::KIND_KERR;
+    // integrator probes on a grid of the given stride (images of at least 2 x 2 pixels)
+    gt::sg::ProbeGrid pg = {};
+    if (probe_stride > 0 && c->res_x >= 2 && c->res_y >= 2) {
+        pg.stride = probe_stride;
+        pg.nx = (c->res_x - 2) / probe_stride + 2;
+        pg.ny = (c->res_y - 2) / probe_stride + 2;
+        pg.tol = probe_tol;
+        const int64_t np = (int64_t)pg.nx * pg.ny;
+        const size_t per = 8 + 4 * 8 + 4 + 1 + sizeof(gt::sg::ProbeRec);
+        if (c->probe_cap < np) {
+            cudaStreamSynchronize(c->stream);
+            cudaFree(c->d_probe);
+            c->d_probe = nullptr;
+            c->probe_cap = 0;
+            cudaError_t e = cudaMalloc(&c->d_probe, np * per + 256);
+            if (e != cudaSuccess) return cuda_code(e);
+            c->probe_cap = np;
+        }
+        int64_t *pix = (int64_t *)c->d_probe;
+        double *pt = (double *)(pix + np), *pr = pt + np, *pth = pr + np, *pph = pth + np;
+        gt::sg::ProbeRec *rec = (gt::sg::ProbeRec *)(pph + np);
+        uint32_t *pns = (uint32_t *)(rec + np);
+        uint8_t *pst = (uint8_t *)(pns + np);
+        rc = gt::sg::probe_pixels(c->d_cam, pg, pix, c->stream);
+        if (rc == GT_OK)
+            rc = run_trace(c, c->d_cam, 1, kind, 0, np, n_steps, sp, mode, pt, pr, pth, pph, pst,
+                           pns, pix, nullptr, true);
+        if (rc == GT_OK)
+            rc = gt::sg::probe_records(s, c->d_cam, pix, (int)np, pt, pr, pth, pph, pst, pns, rec,
+                                       t, r, th, ph, status, nsteps, c->stream);
+        if (rc != GT_OK) return rc;
+        pg.rec = rec;
+        if (n_probes) *n_probes = np;
+    } else if (n_probes) {
+        *n_probes = 0;
+    }
     unsigned long long *d_nfb = c->d_scratch + gt::SCR_TO32; // free until the fallback trace
     cudaError_t err = cudaMemsetAsync(d_nfb, 0, sizeof(unsigned long long), c->stream);
     if (err != cudaSuccess) return cuda_code(err);
-    rc = gt::sg::infer_chunks(s, c->d_cam, n_pix, tau, band, dir_tol, t, r, th, ph, status,
+    rc = gt::sg::infer_chunks(s, c->d_cam, n_pix, tau, band, dir_tol, pg, t, r, th, ph, status,
                               nsteps, c->d_fallback, d_nfb, c->stream);
     if (rc != GT_OK) return rc;
     unsigned long long nfb = 0;
@@ -870,7 +919,6 @@ int gt_surrogate_infer(gt_ctx *c, gt_surrogate *s, float tau, double band, float
     if (err != cudaSuccess) return cuda_code(err);
     if (n_fallback) *n_fallback = (int64_t)nfb;
     if (nfb == 0) return GT_OK;
-    const int kind = (c->Q != 0.0) ? gt::KIND_MN : gt::KIND_KERR;
     return run_trace(c, c->d_cam, 1, kind, 0, (int64_t)nfb, n_steps, sp, mode, t, r, th, ph,
                      status, nsteps, c->d_fallback, nullptr);
 }

@@ -127,14 +127,15 @@ __global__ void features_kernel(int64_t n, int64_t row0, const double *alpha, co
         for (int j = 0; j < 16; j++) X0T[j * n + r] = __float2bfloat16(f[j]);
 }
 
-// features of camera pixels [pix0, pix0 + n) (flat j*res_x + i)
+// features of camera pixels [pix0, pix0 + n) (flat j*res_x + i), or of the listed pixels
+// pixels[pix0 + r]
 __global__ void camera_features_kernel(int64_t n, int64_t pix0, const CamDesc *cam, Norm nm,
-                                       __nv_bfloat16 *X0)
+                                       __nv_bfloat16 *X0, const int64_t *pixels = nullptr)
 {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     const CamDesc &c = *cam;
-    const int64_t pix = pix0 + r;
+    const int64_t pix = pixels ? pixels[pix0 + r] : pix0 + r;
     const int i = (int)(pix % c.res_x), j = (int)(pix / c.res_x);
     const double al = c.res_x > 1 ? c.H * (double)(2 * i - (c.res_x - 1)) / (double)(c.res_x - 1) : 0.0;
     const double bt = c.res_y > 1 ? c.V * (double)(2 * j - (c.res_y - 1)) / (double)(c.res_y - 1) : 0.0;
@@ -274,32 +275,145 @@ __device__ double kerr_rmin(const CamDesc &c, const Ray64 &p)
     return best;
 }
 
-// Decide per pixel: confident surrogate answer, or fall back to the integrator.
+// Probe pixel columns: k stride for k < n - 1, and the last column (res - 1).
+__device__ __forceinline__ int probe_coord(int k, int stride, int n, int res)
+{
+    return k < n - 1 ? k * stride : res - 1;
+}
+
+__device__ __forceinline__ bool is_probe(int i, int j, const ProbeGrid &pg, int res_x, int res_y)
+{
+    return (i % pg.stride == 0 || i == res_x - 1) && (j % pg.stride == 0 || j == res_y - 1);
+}
+
+__global__ void probe_pixels_kernel(const CamDesc *cam, ProbeGrid pg, int64_t *pix)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= pg.nx * pg.ny) return;
+    const int kx = k % pg.nx, ky = k / pg.nx;
+    const int i = probe_coord(kx, pg.stride, pg.nx, cam->res_x);
+    const int j = probe_coord(ky, pg.stride, pg.ny, cam->res_y);
+    pix[k] = (int64_t)j * cam->res_x + i;
+}
+
+// Probe records from the integrator's results and the network's outputs on the probes.
+__global__ void probe_record_kernel(int n, const float *Z5, const uint8_t *st, const double *th,
+                                    const double *ph, ProbeRec *rec)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float *z = Z5 + (int64_t)k * 16;
+    ProbeRec o;
+    o.exact = st[k];
+    o.net_esc = z[0] > 0.0f ? 1 : 0;
+    o.pad[0] = o.pad[1] = 0;
+    if (st[k] == GT_RAY_ESCAPED) {
+        const double s = sin(th[k]);
+        o.err[0] = (float)(s * cos(ph[k])) - z[1];
+        o.err[1] = (float)(s * sin(ph[k])) - z[2];
+        o.err[2] = (float)cos(th[k]) - z[3];
+    } else {
+        o.err[0] = o.err[1] = o.err[2] = 0.0f;
+    }
+    rec[k] = o;
+}
+
+// The probes' exact results into the image (their pixels are neither network nor fallback).
+__global__ void scatter_probes_kernel(int n, const int64_t *pix, const double *pt, const double *pr,
+                                      const double *pth, const double *pph, const uint8_t *pst,
+                                      const uint32_t *pns, double *t, double *r, double *th,
+                                      double *ph, uint8_t *status, uint32_t *nsteps)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t q = pix[k];
+    t[q] = pt[k];
+    r[q] = pr[k];
+    th[q] = pth[k];
+    ph[q] = pph[k];
+    status[q] = pst[k];
+    nsteps[q] = pns[k];
+}
+
+// Decide per pixel: confident surrogate answer, or fall back to the integrator.  With
+// probes, a pixel is taken from the network only inside a probe cell whose four corners
+// the integrator and the network classify alike -- all escaped, or all captured
+// (HORIZON) -- and, for escaped ones, whose corner error vectors differ by less than
+// pg.tol; its end direction is the network's plus the bilinear interpolation of the
+// corners' error vectors (the integrator correcting the network where it measured it).
 __global__ void gate_kernel(int64_t n, int64_t pix0, const CamDesc *cam, const float *Z5, float tau,
-                            double band, float dir_tol, double *t, double *r, double *th,
-                            double *ph, uint8_t *status, uint32_t *nsteps, int64_t *fallback,
-                            unsigned long long *n_fallback)
+                            double band, float dir_tol, ProbeGrid pg, double *t, double *r,
+                            double *th, double *ph, uint8_t *status, uint32_t *nsteps,
+                            int64_t *fallback, unsigned long long *n_fallback)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool fb = false;
     int64_t pix = pix0 + k;
     if (k < n) {
+        const int res_x = cam->res_x, res_y = cam->res_y;
+        const int i = (int)(pix % res_x), j = (int)(pix / res_x);
         const float *z = Z5 + k * 16;
         const float logit = z[0];
-        bool ring = false;
-        if (band > 0.0 && cam->st.kind == KIND_KERR) {
-            Ray64 p;
-            camera_init(*cam, pix, p);
-            ring = fabs(kerr_rmin(*cam, p)) < band;
+        float nx = z[1], ny = z[2], nz = z[3];
+        bool skip = false; // a probe: written by the integrator pass
+        if (pg.stride > 0) {
+            if (is_probe(i, j, pg, res_x, res_y)) {
+                skip = true;
+            } else {
+                const int kx = min(i / pg.stride, pg.nx - 2), ky = min(j / pg.stride, pg.ny - 2);
+                const int x0 = probe_coord(kx, pg.stride, pg.nx, res_x);
+                const int x1 = probe_coord(kx + 1, pg.stride, pg.nx, res_x);
+                const int y0 = probe_coord(ky, pg.stride, pg.ny, res_y);
+                const int y1 = probe_coord(ky + 1, pg.stride, pg.ny, res_y);
+                const ProbeRec &c00 = pg.rec[ky * pg.nx + kx], &c01 = pg.rec[ky * pg.nx + kx + 1];
+                const ProbeRec &c10 = pg.rec[(ky + 1) * pg.nx + kx];
+                const ProbeRec &c11 = pg.rec[(ky + 1) * pg.nx + kx + 1];
+                const bool esc4 = c00.exact == GT_RAY_ESCAPED && c01.exact == GT_RAY_ESCAPED &&
+                                  c10.exact == GT_RAY_ESCAPED && c11.exact == GT_RAY_ESCAPED &&
+                                  c00.net_esc && c01.net_esc && c10.net_esc && c11.net_esc;
+                const bool cap4 = c00.exact == GT_RAY_HORIZON && c01.exact == GT_RAY_HORIZON &&
+                                  c10.exact == GT_RAY_HORIZON && c11.exact == GT_RAY_HORIZON &&
+                                  !c00.net_esc && !c01.net_esc && !c10.net_esc && !c11.net_esc;
+                if (logit > 0.0f) {
+                    float sp = 0.0f, sq = 0.0f;
+#pragma unroll
+                    for (int m = 0; m < 3; m++) {
+                        const float a = c00.err[m] - c11.err[m], b = c01.err[m] - c10.err[m];
+                        sp = fmaf(a, a, sp);
+                        sq = fmaf(b, b, sq);
+                    }
+                    if (!esc4 || !(fmaxf(sp, sq) < pg.tol * pg.tol)) {
+                        fb = true;
+                    } else {
+                        const float tx = (float)(i - x0) / (float)(x1 - x0);
+                        const float ty = (float)(j - y0) / (float)(y1 - y0);
+                        const float w00 = (1.0f - tx) * (1.0f - ty), w01 = tx * (1.0f - ty);
+                        const float w10 = (1.0f - tx) * ty, w11 = tx * ty;
+                        nx += w00 * c00.err[0] + w01 * c01.err[0] + w10 * c10.err[0] + w11 * c11.err[0];
+                        ny += w00 * c00.err[1] + w01 * c01.err[1] + w10 * c10.err[1] + w11 * c11.err[1];
+                        nz += w00 * c00.err[2] + w01 * c01.err[2] + w10 * c10.err[2] + w11 * c11.err[2];
+                    }
+                } else if (!cap4) {
+                    fb = true;
+                }
+            }
         }
-        const float nx = z[1], ny = z[2], nz = z[3];
-        const float nn = sqrtf(nx * nx + ny * ny + nz * nz);
-        // an escaping prediction whose direction vector is not of unit length is unsettled
-        const bool loose = dir_tol > 0.0f && logit > 0.0f && !(fabsf(nn - 1.0f) <= dir_tol);
-        fb = fabsf(logit) < tau || ring || loose;
-        if (!fb) {
+        if (!skip && !fb) {
+            bool ring = false;
+            if (band > 0.0 && cam->st.kind == KIND_KERR) {
+                Ray64 p;
+                camera_init(*cam, pix, p);
+                ring = fabs(kerr_rmin(*cam, p)) < band;
+            }
+            const float nn = sqrtf(z[1] * z[1] + z[2] * z[2] + z[3] * z[3]);
+            // an escaping prediction whose direction vector is not of unit length is unsettled
+            const bool loose = dir_tol > 0.0f && logit > 0.0f && !(fabsf(nn - 1.0f) <= dir_tol);
+            fb = fabsf(logit) < tau || ring || loose;
+        }
+        if (!skip && !fb) {
             if (logit > 0.0f) {
-                th[pix] = acos(fminf(fmaxf(nz / nn, -1.0f), 1.0f));
+                const float nc = sqrtf(nx * nx + ny * ny + nz * nz);
+                th[pix] = acos(fminf(fmaxf(nz / nc, -1.0f), 1.0f));
                 ph[pix] = atan2(ny, nx);
                 status[pix] = GT_RAY_ESCAPED;
             } else {
@@ -664,6 +778,14 @@ int gt_surrogate_get_params(gt_surrogate *s, float *host, int64_t n)
                                                                                            : GT_ERR_CUDA;
 }
 
+int gt_surrogate_get_grads(gt_surrogate *s, float *host, int64_t n)
+{
+    if (!s || !host || n != s->n_params) return GT_ERR_INVALID_ARG;
+    Dev d(s->device);
+    return cudaMemcpy(host, s->g, n * sizeof(float), cudaMemcpyDeviceToHost) == cudaSuccess ? GT_OK
+                                                                                           : GT_ERR_CUDA;
+}
+
 int gt_surrogate_set_params(gt_surrogate *s, const float *host, int64_t n)
 {
     if (!s || !host || n != s->n_params) return GT_ERR_INVALID_ARG;
@@ -779,8 +901,9 @@ namespace gt {
 namespace sg {
 
 int infer_chunks(gt_surrogate *s, const CamDesc *d_cam, int64_t n_pix, float tau, double band,
-                 float dir_tol, double *t, double *r, double *th, double *ph, uint8_t *status,
-                 uint32_t *nsteps, int64_t *d_fallback, unsigned long long *d_nfb, cudaStream_t st)
+                 float dir_tol, const ProbeGrid &pg, double *t, double *r, double *th, double *ph,
+                 uint8_t *status, uint32_t *nsteps, int64_t *d_fallback, unsigned long long *d_nfb,
+                 cudaStream_t st)
 {
     const int64_t chunk = 1 << 19;
     int rc = ensure_ws(s, n_pix < chunk ? n_pix : chunk);
@@ -791,10 +914,40 @@ int infer_chunks(gt_surrogate *s, const CamDesc *d_cam, int64_t n_pix, float tau
         cudaError_t e = forward(s, (int)B, st, false);
         if (e != cudaSuccess) return GT_ERR_CUDA;
         gate_kernel<<<blocks_for(B), 256, 0, st>>>(B, p0, d_cam, s->Z[N_LAYERS - 1], tau, band,
-                                                   dir_tol, t, r, th, ph, status, nsteps,
+                                                   dir_tol, pg, t, r, th, ph, status, nsteps,
                                                    d_fallback, d_nfb);
         if (cudaGetLastError() != cudaSuccess) return GT_ERR_CUDA;
     }
+    return check_err(s, st);
+}
+
+int probe_pixels(const CamDesc *d_cam, const ProbeGrid &pg, int64_t *d_pix, cudaStream_t st)
+{
+    const int n = pg.nx * pg.ny;
+    probe_pixels_kernel<<<blocks_for(n), 256, 0, st>>>(d_cam, pg, d_pix);
+    return cudaGetLastError() == cudaSuccess ? GT_OK : GT_ERR_CUDA;
+}
+
+// The network on the probe pixels, the probe records, and the probes' exact results
+// written into the image.
+int probe_records(gt_surrogate *s, const CamDesc *d_cam, const int64_t *d_pix, int n,
+                  const double *pt, const double *pr, const double *pth, const double *pph,
+                  const uint8_t *pst, const uint32_t *pns, ProbeRec *rec, double *t, double *r,
+                  double *th, double *ph, uint8_t *status, uint32_t *nsteps, cudaStream_t st)
+{
+    const int64_t chunk = 1 << 19;
+    int rc = ensure_ws(s, n < chunk ? n : chunk);
+    if (rc != GT_OK) return rc;
+    for (int64_t p0 = 0; p0 < n; p0 += chunk) {
+        const int64_t B = n - p0 < chunk ? n - p0 : chunk;
+        camera_features_kernel<<<blocks_for(B), 256, 0, st>>>(B, p0, d_cam, s->norm, s->X[0], d_pix);
+        if (forward(s, (int)B, st, false) != cudaSuccess) return GT_ERR_CUDA;
+        probe_record_kernel<<<blocks_for(B), 256, 0, st>>>((int)B, s->Z[N_LAYERS - 1], pst + p0,
+                                                           pth + p0, pph + p0, rec + p0);
+    }
+    scatter_probes_kernel<<<blocks_for(n), 256, 0, st>>>(n, d_pix, pt, pr, pth, pph, pst, pns, t, r,
+                                                         th, ph, status, nsteps);
+    if (cudaGetLastError() != cudaSuccess) return GT_ERR_CUDA;
     return check_err(s, st);
 }
 

@@ -33,7 +33,7 @@ EXPORTS = ("gt_create", "gt_destroy", "gt_set_stream", "gt_set_spacetime", "gt_s
            "gt_trace_rays", "gt_autotune", "gt_surrogate_num_params", "gt_surrogate_create",
            "gt_surrogate_destroy", "gt_surrogate_get_params", "gt_surrogate_set_params",
            "gt_surrogate_eval", "gt_surrogate_grad", "gt_surrogate_train", "gt_surrogate_infer",
-           "gt_trace_disk", "gt_trace_states", "gt_strerror")
+           "gt_trace_disk", "gt_trace_states", "gt_surrogate_get_grads", "gt_strerror")
 
 
 class GeotraceError(RuntimeError):
@@ -111,8 +111,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.gt_surrogate_eval.argtypes = [vp, vp, i64] + [vp] * 5 + [vp]
     lib.gt_surrogate_grad.argtypes = [vp, vp, i64] + [vp] * 8 + [ctypes.c_float, vp, vp]
     lib.gt_surrogate_train.argtypes = [vp, vp, ctypes.POINTER(TrainCfg), i64] + [vp] * 8 + [vp]
-    lib.gt_surrogate_infer.argtypes = [vp, vp, ctypes.c_float, d, ctypes.c_float, i64, d, i] + out6 + [
-        ctypes.POINTER(i64)]
+    lib.gt_surrogate_infer.argtypes = [vp, vp, ctypes.c_float, d, ctypes.c_float, i,
+                                       ctypes.c_float, i64, d, i] + out6 + [
+        ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    lib.gt_surrogate_get_grads.argtypes = [vp, vp, i64]
     lib.gt_strerror.argtypes = [i]
     lib.gt_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -394,17 +396,29 @@ class Surrogate:
                                            losses.ctypes.data), "gt_surrogate_train")
         return losses
 
+    def get_grads(self) -> np.ndarray:
+        out = np.empty(self.n_params, dtype=np.float32)
+        _check(self.lib.gt_surrogate_get_grads(self.h, out.ctypes.data, self.n_params),
+               "gt_surrogate_get_grads")
+        return out
+
     def infer(self, tracer: "Tracer", tau: float, band: float, n_steps: int,
               step_precision: float, mode: int = MODE_FP32_MIXED, out: Optional[dict] = None,
-              dir_tol: float = 0.0):
+              dir_tol: float = 0.0, probe_stride: int = 0, probe_tol: float = 0.0,
+              with_probes: bool = False):
+        """gt_surrogate_infer; returns (outputs, integrated pixels besides the probes) or,
+        with with_probes, (outputs, fallback pixels, probe pixels)."""
         n = tracer.res[0] * tracer.res[1]
         if out is None:
             out = tracer.alloc_outputs(n)
-        nfb = ctypes.c_int64()
+        nfb, npr = ctypes.c_int64(), ctypes.c_int64()
         _check(self.lib.gt_surrogate_infer(tracer.ctx, self.h, float(tau), float(band),
-                                           float(dir_tol), int(n_steps), float(step_precision),
-                                           int(mode),
+                                           float(dir_tol), int(probe_stride), float(probe_tol),
+                                           int(n_steps), float(step_precision), int(mode),
                                            *[_ptr(out[k]) for k in ("t", "r", "th", "ph",
                                                                     "status", "nsteps")],
-                                           ctypes.byref(nfb)), "gt_surrogate_infer")
+                                           ctypes.byref(nfb), ctypes.byref(npr)),
+               "gt_surrogate_infer")
+        if with_probes:
+            return out, nfb.value, npr.value
         return out, nfb.value

@@ -14,6 +14,7 @@ Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|referen
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -153,7 +154,7 @@ def oracle_rate(wl: W.Workload, target_s: float = 12.0, seed: int = 3) -> dict:
         dt = time.perf_counter() - t0
     steps = float(np.sum(out["nsteps"].astype(np.float64)))
     return {"steps_per_s": steps / dt, "rays_per_s": n / dt, "seconds": dt, "rays": int(n),
-            "steps": steps, "cores": threads,
+            "steps": steps, "cores": threads, "pixels": pix, "out": out,
             "sample": f"{n} seeded pixels of the {cam.res_x}x{cam.res_y} {wl.name} camera, "
                       f"{wl.n_steps} max steps each, {threads} threads"}
 
@@ -218,15 +219,17 @@ def leg_batch(tr, geotrace, args, torch):
     tr.set_spacetime(rep.M, rep.S, rep.Q)
     tr.set_camera(rep.r0, rep.theta0, rep.fov_deg, 256, 256)
     tr.set_options()
-    b, k, v = tr.autotune(geotrace.MODE_FP32_MIXED, trial_rays=1 << 16, trial_steps=300,
-                          cache_path=os.path.join(ROOT, "paper_2310_15183_gb300", "_build", "autotune.txt"))
+    b, k, rpt, v = tr.autotune(geotrace.MODE_FP32_MIXED, trial_rays=1 << 16, trial_steps=300,
+                               cache_path=os.path.join(ROOT, "paper_2310_15183_gb300", "_build",
+                                                       "autotune.txt"))
     res = {"cameras": len(cams), "rays": n, "n_steps": 500000,
            "sides": [min(c.res_x for c in cams), max(c.res_x for c in cams)],
            "scale": f"camera sides divided by {args.batch_scale}",
-           "autotuned": {"block_size": b, "blocks_per_sm": k, "trial_steps_per_s": v}}
+           "autotuned": {"block_size": b, "blocks_per_sm": k, "rays_per_thread": rpt,
+                         "trial_steps_per_s": v}}
     out = tr.alloc_outputs(n)
     for label, flags in (("graph", geotrace.FLAG_GRAPH), ("rounds", 0)):
-        tr.set_options(block_size=b, blocks_per_sm=k, flags=flags)
+        tr.set_options(block_size=b, blocks_per_sm=k, flags=flags, rays_per_thread=rpt)
         tr.trace_batch(cams, 500000, 1.5e-4, geotrace.MODE_FP32_MIXED, out=out)  # warm-up/capture
         _, t = _timed(torch, tr.stream,
                       lambda: tr.trace_batch(cams, 500000, 1.5e-4, geotrace.MODE_FP32_MIXED, out=out))
@@ -409,6 +412,216 @@ def leg_sweep(tr, geotrace, args, torch):
     return res
 
 
+def leg_paper(tr, geotrace, args, torch):
+    """The paper's own method on GB300: the listing's numerics (forward-difference metric
+    derivatives, float32 I/O, 0.1667 weights, v^phi = alpha; FP64 arithmetic) on the
+    listing's camera (r0 = 16M, theta0 = pi/2, FOV 75 deg, 1000x1000) at its 500,000-step
+    cap, Kerr (S = 0.24, Q = 0) and the listing's Manko-Novikov (q = 2), on a seeded pixel
+    sample, seconds per megapixel extrapolated; beside this build's exact FP64 and
+    FP32-mixed paths on the same pixels.  The paper quotes ~300 s (Kerr) and 1,200-3,000 s
+    (Manko-Novikov) per megapixel on its GPU."""
+    import numpy as np
+    res = {}
+    for name, (S, Q, n_pix) in {"kerr": (0.24, 0.0, 16384), "mn": (0.24, 2.0, 2048)}.items():
+        cam = W.Camera(M=0.5, S=S, Q=Q, r0=8.0, theta0=math.pi / 2, fov_deg=75.0,
+                       res_x=1000, res_y=1000)
+        pix = torch.tensor(W.sample_pixels(cam.n_rays, n_pix, seed=51), device="cuda")
+        tr.set_spacetime(cam.M, cam.S, cam.Q)
+        tr.set_camera(cam.r0, cam.theta0, cam.fov_deg, cam.res_x, cam.res_y)
+        r = {"sample_pixels": n_pix}
+        for label, flags, mode in (("paper_numerics_fp64", geotrace.FLAGS_PAPER, geotrace.MODE_FP64),
+                                   ("exact_fp64", 0, geotrace.MODE_FP64),
+                                   ("exact_fp32_mixed", 0, geotrace.MODE_FP32_MIXED)):
+            tr.set_options(flags=flags)
+            out, t = _timed(torch, tr.stream, lambda: tr.trace_pixels(pix, 500000, 1.5e-4, mode))
+            st = _steps(out)
+            r[label] = {"seconds": t, "seconds_per_mpx": t * 1e6 / n_pix, "steps_per_s": st / t}
+        res[name] = r
+    tr.set_options()
+    res["paper_seconds_per_mpx"] = {"kerr": 300, "mn": [1200, 3000],
+                                    "hardware": "unnamed 2016 consumer GPU (paper, Sec. 4)"}
+    return res
+
+
+def leg_mn_sweep(tr, geotrace, args, torch):
+    """Inclination sweep of the listing's Manko-Novikov spacetime (q = 2, S = 0.24, r0 =
+    30M, FOV 75 deg) at the 500,000-step cap, frames theta0 = 5, 35, 62, 90 deg, on a
+    128x128 subsample (pixels 8m+4) of a 1024x1024 camera, FP32-mixed; status counts and
+    the FP64-zone share of the steps."""
+    import numpy as np
+    jj, ii = np.meshgrid(np.arange(4, 1024, 8), np.arange(4, 1024, 8), indexing="ij")
+    pix = torch.tensor((jj * 1024 + ii).ravel().astype(np.int64), device="cuda")
+    res = {}
+    for th_deg in (5.0, 35.0, 62.0, 90.0):
+        tr.set_spacetime(0.5, 0.24, 2.0)
+        tr.set_camera(15.0, th_deg * W.DEG, 75.0, 1024, 1024)
+        tr.set_options()
+        out, t = _timed(torch, tr.stream,
+                        lambda: tr.trace_pixels(pix, 500000, 1.5e-4, geotrace.MODE_FP32_MIXED))
+        zone = tr.zone_steps()
+        steps = _steps(out)
+        st = out["status"].cpu().numpy()
+        res[f"theta0_{th_deg:g}"] = {
+            "seconds": t, "steps_per_s": steps / t, "seconds_per_mpx": t * 1e6 / pix.numel(),
+            "status_counts": {str(a): int(b) for a, b in zip(*np.unique(st, return_counts=True))},
+            "fp64_zone_step_fraction": zone / steps}
+    res["subsample"] = "128x128 pixels (8m+4) of 1024x1024"
+    return res
+
+
+# ------------------------------------------------------------------ accuracy and extra modes
+def great_circle(th1, ph1, th2, ph2):
+    import numpy as np
+    a = np.sin((th2 - th1) / 2) ** 2 + np.sin(th1) * np.sin(th2) * np.sin((ph2 - ph1) / 2) ** 2
+    return 2 * np.arcsin(np.sqrt(np.clip(a, 0, 1)))
+
+
+def accuracy(got: dict, ref: dict) -> dict:
+    """Error of a GPU result against the FP64 oracle (or the FP64 GPU path) on the same
+    rays: classification agreement, end-angle error of rays both call escaped, and the
+    largest relative error of t, r, theta, phi on rays of equal status."""
+    import numpy as np
+    same = got["status"] == ref["status"]
+    esc = same & (ref["status"] == 0)
+    ang = great_circle(got["th"][esc], got["ph"][esc], ref["th"][esc], ref["ph"][esc])
+    rel = 0.0
+    for k in ("t", "r", "th", "ph"):
+        if k in got and k in ref and same.any():
+            e = np.abs(got[k][same] - ref[k][same]) / np.maximum(1.0, np.abs(ref[k][same]))
+            rel = max(rel, float(np.nanmax(e)))
+    return {"rays": int(ref["status"].size), "classification_agreement": float(same.mean()),
+            "angle_err_max": float(ang.max()) if ang.size else 0.0,
+            "angle_err_median": float(np.median(ang)) if ang.size else 0.0,
+            "max_rel_err": rel}
+
+
+def host_sample(out: dict, idx) -> dict:
+    import numpy as np
+    res = {}
+    for k, v in out.items():
+        a = v.cpu().numpy()
+        if k == "nsteps":
+            a = a.view(np.uint32)
+        res[k] = a[idx]
+    return res
+
+
+def oracle_sample(cam, n_steps, sp, pixels) -> dict:
+    """The FP64 CPU oracle on listed pixels (a CPU-baseline sample; also the reference the
+    GPU results of that sample are judged against)."""
+    import oracle
+    return oracle.trace_image(cam.M, cam.S, cam.Q, cam.r0, cam.theta0, cam.fov_deg, cam.res_x,
+                              cam.res_y, n_steps, sp, pixels=pixels)
+
+
+def mode_terminating(tr, geotrace, torch) -> dict:
+    """The paper's terminating workloads at the listing's 500,000-step cap, FP32-mixed:
+    the whole 1000x1000 Kerr a = 0.9M image, and a seeded pixel sample of the listing's
+    Manko-Novikov spacetime (its FP64 zone bounds it); each with its error against the
+    FP64 oracle on a pixel sample and the share of steps taken in the FP64 zone."""
+    import numpy as np
+    res = {}
+    cap, sp = 500000, 1.5e-4
+    kerr = W.Camera(M=0.5, S=0.9 * 0.25, Q=0.0, r0=15.0, theta0=80 * W.DEG, fov_deg=75.0,
+                    res_x=1000, res_y=1000)
+    cases = (("kerr1000_T", kerr, None, 32), ("mn1000_T", W.MN_1000, 4096, 16))
+    for name, cam, n_sample, n_judge in cases:
+        tr.set_spacetime(cam.M, cam.S, cam.Q)
+        tr.set_camera(cam.r0, cam.theta0, cam.fov_deg, cam.res_x, cam.res_y)
+        tr.set_options()
+        if n_sample is None:
+            pix = None
+            run = lambda: tr.trace(cap, sp, geotrace.MODE_FP32_MIXED)
+            n = cam.n_rays
+        else:
+            pix = W.sample_pixels(cam.n_rays, n_sample, seed=31)
+            dpix = torch.tensor(pix, device="cuda")
+            run = lambda: tr.trace_pixels(dpix, cap, sp, geotrace.MODE_FP32_MIXED)
+            n = n_sample
+        out, t = _timed(torch, tr.stream, run)
+        zone = tr.zone_steps()
+        steps = _steps(out)
+        st = out["status"].cpu().numpy()
+        judge = W.sample_pixels(n, n_judge, seed=32)
+        got = host_sample(out, judge)
+        t0 = time.perf_counter()
+        ref = oracle_sample(cam, cap, sp, judge if pix is None else pix[judge])
+        t_cpu = time.perf_counter() - t0
+        res[name] = {
+            "rays": n, "seconds": t, "steps_per_s": steps / t, "rays_per_s": n / t,
+            "seconds_per_mpx": t * 1e6 / n, "mean_steps_per_ray": steps / n,
+            "status_counts": {str(a): int(b) for a, b in zip(*np.unique(st, return_counts=True))},
+            "fp64_zone_step_fraction": zone / steps if steps else 0.0,
+            "sample": "whole image" if pix is None else f"{n} seeded pixels of 1000x1000",
+            "accuracy_vs_oracle": accuracy(got, ref),
+            "cpu_baseline": {"value": float(ref["nsteps"].astype(np.float64).sum()) / t_cpu,
+                             "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
+                             "sample": f"{n_judge} seeded pixels of the GPU sample",
+                             "seconds": t_cpu},
+            "paper_seconds_per_mpx": 300 if name.startswith("kerr") else [1200, 3000]}
+    return res
+
+
+def mode_surrogate(tr, geotrace, torch, args) -> dict:
+    """Surrogate + fallback at a reduced training budget: label sg_default_rays rays with the
+    integrator (FP32-mixed, 500,000-step cap) over the training ranges at r0 = 30M, train,
+    then image a Kerr a = 0.9M, 80 deg camera of sg_default_res^2 pixels with integrator
+    probes every 8 pixels (tolerance 1e-3) and fallback; against integrator-only on the same
+    image (time) and the FP64 integrator on a pixel sample of the network's pixels (error)."""
+    import numpy as np
+    M, r0, sp, cap = 0.5, 15.0, 1.5e-4, 500000
+    host = W.surrogate_samples(args.sg_default_rays, seed=15183, M=M, r0=r0)
+    dev = [torch.tensor(x, dtype=torch.float64, device="cuda") for x in host]
+    lab, t_label = _timed(torch, tr.stream,
+                          lambda: tr.trace_rays(*dev, M, r0, cap, sp, geotrace.MODE_FP32_MIXED))
+    sg = geotrace.Surrogate(0, r0=r0, seed=7)
+    t0 = time.perf_counter()
+    losses = sg.train(tr, dev, [lab["status"], lab["th"], lab["ph"]],
+                      epochs=args.sg_default_epochs, batch=8192, lr=2e-3, dir_weight=100.0)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    res_ = args.sg_default_res
+    cam = W.Camera(M=M, S=0.9 * M * M, Q=0.0, r0=r0, theta0=80 * W.DEG, fov_deg=75.0,
+                   res_x=res_, res_y=res_)
+    tr.set_spacetime(cam.M, cam.S, cam.Q)
+    tr.set_camera(cam.r0, cam.theta0, cam.fov_deg, cam.res_x, cam.res_y)
+    tr.set_options()
+    full = tr.trace(cap, sp, geotrace.MODE_FP32_MIXED)  # warm
+    full, t_full = _timed(torch, tr.stream, lambda: tr.trace(cap, sp, geotrace.MODE_FP32_MIXED))
+    out = tr.alloc_outputs(cam.n_rays)
+    infer = lambda: sg.infer(tr, 2.0, 0.0, cap, sp, geotrace.MODE_FP32_MIXED, out=out,
+                             probe_stride=8, probe_tol=1e-3, with_probes=True)
+    infer()
+    (out, nfb, npr), t_inf = _timed(torch, tr.stream, infer)
+    ns = out["nsteps"].cpu().numpy().view(np.uint32)
+    net = np.flatnonzero(ns == 0)
+    judge = net[W.sample_pixels(net.size, min(4096, net.size), seed=41)]
+    ref = tr.trace_pixels(torch.tensor(judge, device="cuda"), cap, sp, geotrace.MODE_FP64)
+    torch.cuda.synchronize()
+    ref = {k: (v.cpu().numpy().view(np.uint32) if k == "nsteps" else v.cpu().numpy())
+           for k, v in ref.items()}
+    got = host_sample(out, judge)
+    acc = accuracy(got, ref)
+    acc.pop("max_rel_err")  # network pixels carry no t, r
+    # the network alone (no probes, no fallback gates) on the same judged pixels
+    raw = tr.alloc_outputs(cam.n_rays)
+    sg.infer(tr, 0.0, 0.0, cap, sp, geotrace.MODE_FP32_MIXED, out=raw)
+    acc_raw = accuracy(host_sample(raw, judge), ref)
+    acc_raw.pop("max_rel_err")
+    sg.close()
+    return {"train_rays": args.sg_default_rays, "epochs": args.sg_default_epochs,
+            "label_seconds": t_label, "train_seconds": t_train,
+            "loss_first_last": [float(losses[0]), float(losses[-1])],
+            "image": [cam.res_x, cam.res_y], "seconds": t_inf,
+            "rays_per_s": cam.n_rays / t_inf,
+            "integrator_only_seconds": t_full, "speedup_vs_integrator_only": t_full / t_inf,
+            "probe_pixels": npr, "fallback_pixels": nfb,
+            "network_pixel_fraction": net.size / cam.n_rays,
+            "gates": {"tau": 2.0, "probe_stride": 8, "probe_tol": 1e-3},
+            "accuracy_vs_fp64": acc, "network_alone_vs_fp64": acc_raw,
+            "judge": f"FP64 integrator on {judge.size} seeded network pixels"}
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -418,10 +631,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mn1000", choices=sorted(W.WORKLOADS))
     ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--fp64-rows", type=int, default=64,
-                    help="image rows traced by the FP64 plain leg (0 = skip)")
+    ap.add_argument("--fp64-rows", type=int, default=-1,
+                    help="image rows traced by the FP64 plain leg (-1 = the whole image, 0 = skip)")
+    ap.add_argument("--no-terminating", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--sg-default-rays", type=int, default=1 << 21)
+    ap.add_argument("--sg-default-epochs", type=int, default=80)
+    ap.add_argument("--sg-default-res", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--legs", default="", help="extra legs: batch,surrogate,sweep (comma list)")
+    ap.add_argument("--legs", default="",
+                    help="extra legs: batch,surrogate,sweep,gemm,paper,mn_sweep (comma list)")
     ap.add_argument("--sg-samples", type=int, default=1 << 22)
     ap.add_argument("--sg-epochs", type=int, default=120)
     ap.add_argument("--sg-batch", type=int, default=8192)
@@ -525,14 +744,26 @@ def main():
                 "flops_per_rk4_step": flops_per_step,
                 "flop_convention": "add/mul 1, fma 2, div/rsqrt/exp 1, sincos 2 (opcount.cpp)"}
 
-    # ---------------- FP64 plain leg on a band of image rows
+    # ---------------- the CPU oracle on a bounded sample (rank 0, N = 1): the CPU baseline,
+    # and the FP64 reference every GPU result of this workload is judged against
+    cpu, acc_pix, acc_ref = None, None, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = oracle_rate(wl)
+        cpu = {"value": r["steps_per_s"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+               "sample": r["sample"], "rays_per_s": r["rays_per_s"], "seconds": r["seconds"]}
+        acc_pix, acc_ref = r["pixels"], r["out"]
     modes = {}
-    if args.fp64_rows > 0 and mode == geotrace.MODE_FP32_MIXED:
-        rows = min(args.fp64_rows, cam.res_y)
+    if acc_ref is not None:
+        modes["fp32_mixed"] = {"accuracy_vs_oracle": accuracy(host_sample(out, acc_pix), acc_ref)}
+
+    # ---------------- FP64 plain leg (the whole image unless --fp64-rows limits it)
+    if args.fp64_rows != 0 and mode == geotrace.MODE_FP32_MIXED:
+        rows = cam.res_y if args.fp64_rows < 0 else min(args.fp64_rows, cam.res_y)
         first = (cam.res_y // 2 - rows // 2) * cam.res_x
         cnt = rows * cam.res_x
         o64 = tr.alloc_outputs(cnt)
-        tr.trace_range(first, cnt, wl.n_steps, wl.step_precision, geotrace.MODE_FP64, o64)
+        tr.trace_range(first + (rows // 2) * cam.res_x, cam.res_x, wl.n_steps, wl.step_precision,
+                       geotrace.MODE_FP64, o64)  # warm-up: one row
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(stream):
@@ -545,10 +776,28 @@ def main():
         f64 = counts[f"{kind}_step_flops"]
         modes["fp64_plain"] = {
             "steps_per_s": s64 / t64, "rays_per_s": cnt / t64, "seconds": t64,
-            "sample": f"{rows} central rows ({cnt} rays) of the same camera",
-            "achieved_tflops": f64 * s64 / t64 / 1e12, "frac_of_fp64_nominal": f64 * s64 / t64 / FP64_NOMINAL}
-        modes["fp32_mixed"] = {"steps_per_s": value / world, "rays_per_s": rays_per_s / world}
+            "sample": "the whole image" if rows == cam.res_y else
+                      f"{rows} central rows ({cnt} rays) of the same camera",
+            "achieved_tflops": f64 * s64 / t64 / 1e12, "frac_of_fp64_nominal": f64 * s64 / t64 / FP64_NOMINAL,
+            "flops_per_rk4_step": f64}
+        if acc_ref is not None and rows == cam.res_y:
+            modes["fp64_plain"]["accuracy_vs_oracle"] = accuracy(host_sample(o64, acc_pix), acc_ref)
+        modes.setdefault("fp32_mixed", {}).update(
+            {"steps_per_s": value / world, "rays_per_s": rays_per_s / world})
         modes["speedup_mixed_over_fp64"] = (value / world) / (s64 / t64)
+
+    # ---------------- the paper's terminating workloads and the surrogate (rank 0, N = 1)
+    if rank == 0 and world == 1 and not args.no_terminating:
+        t0 = time.perf_counter()
+        modes["terminating"] = mode_terminating(tr, geotrace, torch)
+        modes["terminating"]["wall_s"] = time.perf_counter() - t0
+    if rank == 0 and world == 1 and not args.no_surrogate:
+        t0 = time.perf_counter()
+        modes["surrogate"] = mode_surrogate(tr, geotrace, torch, args)
+        modes["surrogate"]["wall_s"] = time.perf_counter() - t0
+    tr.set_spacetime(cam.M, cam.S, cam.Q)
+    tr.set_camera(cam.r0, th0, cam.fov_deg, cam.res_x, cam.res_y)
+    tr.set_options()
 
     # ---------------- end to end through the host-pointer C-ABI call
     e2e = None
@@ -575,11 +824,6 @@ def main():
                "h2d_bytes_per_step": desc_bytes, "d2h_bytes_per_step": n * (4 * 8 + 4 + 1),
                "rays_per_s": args.steps * n * world / te}
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r = oracle_rate(wl)
-        cpu = {"value": r["steps_per_s"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
-               "sample": r["sample"], "rays_per_s": r["rays_per_s"], "seconds": r["seconds"]}
 
     legs = {}
     for leg in [x for x in args.legs.split(",") if x]:
@@ -592,6 +836,10 @@ def main():
             legs["sweep"] = leg_sweep(tr, geotrace, args, torch)
         elif leg == "gemm":
             legs["gemm"] = leg_gemm(geotrace, args, torch)
+        elif leg == "paper":
+            legs["paper"] = leg_paper(tr, geotrace, args, torch)
+        elif leg == "mn_sweep":
+            legs["mn_sweep"] = leg_mn_sweep(tr, geotrace, args, torch)
         else:
             raise SystemExit(f"unknown leg {leg}")
         legs[leg]["leg_wall_s"] = time.perf_counter() - t0
@@ -614,6 +862,7 @@ def main():
             "rays_per_s": rays_per_s,
             "status_counts": {str(s): int(c) for s, c in zip(*np.unique(status, return_counts=True))},
             "wall_s_timed_region": wall,
+            "accuracy_vs_oracle": modes.get("fp32_mixed", {}).get("accuracy_vs_oracle"),
             "roofline": roofline, "modes": modes, "e2e": e2e, "cpu_baseline": cpu,
             "clocks": clocks, "gpu_launches": args.steps,
         }

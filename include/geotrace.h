@@ -98,6 +98,10 @@ typedef struct gt_options {
     double r_switch;         /* FP32-mixed: FP64 zone r < r_switch; < 0 = none; 0 = automatic:
                                 none for Kerr, 4M for Manko-Novikov */
     double timeout_seconds;  /* device watchdog (wall clock per launch); 0 = none */
+    int rays_per_thread;     /* FP32-mixed: rays each thread integrates at once, 1 or 2 (two
+                                independent RK4 chains interleaved); 0 = 1.  Two apply to
+                                persistent single-camera traces without the watchdog, ring,
+                                state arrays or per-ray parameters; others use one. */
 } gt_options;
 
 /* One camera of a batch (gt_trace_batch); same meaning as gt_set_spacetime and
@@ -336,16 +340,22 @@ int gt_trace_batch_noalloc(int device, void *cuda_stream, const gt_camera_desc *
 /* Autotuner: time gt_trace_range over `trial_rays` central pixels of the configured
  * camera for `trial_steps` steps with every candidate launch shape (block size in
  * {64, 128, 192, 256} x resident blocks per SM in {1, 2, 3, 4, 6, 8}, within the
- * kernel's occupancy limit), keep the fastest in the context's options, and report it.
+ * kernel's occupancy limit, x rays per thread in {1, 2} for GT_MODE_FP32_MIXED), keep the
+ * fastest in the context's options, and report it (best_rays_per_thread may be NULL).
  * With cache_path != NULL the result is looked up first and appended after tuning,
  * keyed by mode, spacetime kind, SM count and device name (plain text lines).
  * Synchronous.  Errors: GT_ERR_NOT_CONFIGURED, GT_ERR_INVALID_ARG, GT_ERR_CUDA. */
 int gt_autotune(gt_ctx *ctx, int mode, int64_t trial_rays, int64_t trial_steps,
                 double step_precision, const char *cache_path, int *best_block,
-                int *best_blocks_per_sm, double *best_steps_per_s);
+                int *best_blocks_per_sm, int *best_rays_per_thread, double *best_steps_per_s);
 
 /* Wait for all work issued by the context. */
 int gt_sync(gt_ctx *ctx);
+
+/* RK4 steps the last trace of the context took in the FP64 zone of GT_MODE_FP32_MIXED
+ * (0 for FP64 traces and for mixed traces that never entered it); compare with the sum
+ * of nsteps for the zone's share of the work.  Synchronises the context's stream. */
+int gt_get_stats(gt_ctx *ctx, int64_t *zone_steps);
 
 /* Number of streaming multiprocessors of the context's device (for grid sizing). */
 int gt_device_sm_count(gt_ctx *ctx, int *out);

@@ -111,7 +111,22 @@ gt_options effective(const gt_options &o)
     if (e.block_size == 0) e.block_size = 128;
     if (e.blocks_per_sm == 0) e.blocks_per_sm = 4;
     if (e.reproject_every == 0) e.reproject_every = 4096;
+    if (e.rays_per_thread == 0) e.rays_per_thread = 1;
     return e;
+}
+
+// FP32 rounds launches: two rays per thread when asked for and the launch allows it.
+bool use_two(const gt_options &e, const gt::TraceArgs &a, int kind_hint, bool one_shot)
+{
+    return e.rays_per_thread == 2 && !one_shot &&
+           gt::two_rays_supported(a, gt::KMODE_MIXED_FP32, kind_hint);
+}
+
+cudaError_t launch_fp32(const gt_options &e, const gt::TraceArgs &a, int kind_hint, int grid,
+                        bool one_shot, cudaStream_t s)
+{
+    if (use_two(e, a, kind_hint, one_shot)) return gt::launch_trace_two(a, kind_hint, e.block_size, grid, s);
+    return gt::launch_trace(a, gt::KMODE_MIXED_FP32, kind_hint, e.block_size, grid, one_shot, s);
 }
 
 // The listing passes the spacetime parameters to its kernels as float32.
@@ -167,7 +182,10 @@ int grid_for(gt_ctx *c, const gt_options &e, int kmode, int kind_hint, int64_t n
         *grid = g > 0 ? (int)g : 1;
     } else {
         // persistent grid: never more blocks than can be resident at once
-        const int fit = gt::max_blocks_per_sm(kmode, kind_hint, e.block_size);
+        const int fit = (kmode == gt::KMODE_MIXED_FP32 && e.rays_per_thread == 2 &&
+                         (kind_hint == gt::KIND_KERR || kind_hint == gt::KIND_MN))
+                            ? gt::max_blocks_per_sm_two(kind_hint, e.block_size)
+                            : gt::max_blocks_per_sm(kmode, kind_hint, e.block_size);
         *grid = (e.blocks_per_sm < fit ? e.blocks_per_sm : fit) * c->sm_count;
     }
     return GT_OK;
@@ -222,8 +240,7 @@ int build_mixed_graph(gt_ctx *c, const gt::TraceArgs &base, int kind_hint, const
         a.out_items = listA;
         a.out_count = w + gt::SCR_TO64;
         a.out_cap = c->park_cap;
-        if (e1 == cudaSuccess)
-            e1 = gt::launch_trace(a, gt::KMODE_MIXED_FP32, kind_hint, e.block_size, grid32, false, cs);
+        if (e1 == cudaSuccess) e1 = launch_fp32(e, a, kind_hint, grid32, false, cs);
         if (e1 == cudaSuccess) e1 = gt::launch_set_condition(h, w + gt::SCR_TO64, cs);
         cudaStreamCaptureStatus cst;
         const cudaGraphNode_t *deps = nullptr;
@@ -268,8 +285,7 @@ int build_mixed_graph(gt_ctx *c, const gt::TraceArgs &base, int kind_hint, const
         a.in_count = w + gt::SCR_TO32;
         a.out_items = listA;
         a.out_count = w + gt::SCR_TO64;
-        if (e1 == cudaSuccess)
-            e1 = gt::launch_trace(a, gt::KMODE_MIXED_FP32, kind_hint, e.block_size, grid32, false, cs);
+        if (e1 == cudaSuccess) e1 = launch_fp32(e, a, kind_hint, grid32, false, cs);
         if (e1 == cudaSuccess) e1 = gt::launch_set_condition(h, w + gt::SCR_TO64, cs);
         cudaGraph_t done = nullptr;
         err = cudaStreamEndCapture(cs, &done);
@@ -303,8 +319,7 @@ int run_mixed_rounds(gt_ctx *c, gt::TraceArgs &a, int kind_hint, const gt_option
     a.out_count = w + gt::SCR_TO64;
     int rc = grid_for(c, e, gt::KMODE_MIXED_FP32, kind_hint, a.n_fresh, one_shot, &grid);
     if (rc != GT_OK) return rc;
-    cudaError_t err = gt::launch_trace(a, gt::KMODE_MIXED_FP32, kind_hint, e.block_size, grid,
-                                       one_shot, c->stream);
+    cudaError_t err = launch_fp32(e, a, kind_hint, grid, one_shot, c->stream);
     if (err != cudaSuccess) return cuda_code(err);
     for (int round = 0; round < 100000; ++round) {
         unsigned long long parked = 0;
@@ -339,8 +354,7 @@ int run_mixed_rounds(gt_ctx *c, gt::TraceArgs &a, int kind_hint, const gt_option
         if (err != cudaSuccess) return cuda_code(err);
         rc = grid_for(c, e, gt::KMODE_MIXED_FP32, kind_hint, (int64_t)parked, one_shot, &grid);
         if (rc != GT_OK) return rc;
-        err = gt::launch_trace(a, gt::KMODE_MIXED_FP32, kind_hint, e.block_size, grid, one_shot,
-                               c->stream);
+        err = launch_fp32(e, a, kind_hint, grid, one_shot, c->stream);
         if (err != cudaSuccess) return cuda_code(err);
     }
     return GT_ERR_CUDA;
@@ -588,6 +602,7 @@ int gt_set_options(gt_ctx *c, const gt_options *o)
         return GT_ERR_INVALID_ARG;
     if (v.blocks_per_sm < 0 || v.blocks_per_sm > 64) return GT_ERR_INVALID_ARG;
     if (v.reproject_every < 0) return GT_ERR_INVALID_ARG;
+    if (v.rays_per_thread < 0 || v.rays_per_thread > 2) return GT_ERR_INVALID_ARG;
     if (!isfinite(v.r_switch) || !(v.timeout_seconds >= 0.0) || !isfinite(v.timeout_seconds))
         return GT_ERR_INVALID_ARG;
     if (v.flags & ~(GT_FLAG_COMPAT_WEIGHTS | GT_FLAG_COMPAT_CAMERA | GT_FLAG_ONE_SHOT |
@@ -925,7 +940,7 @@ int gt_surrogate_infer(gt_ctx *c, gt_surrogate *s, float tau, double band, float
 
 int gt_autotune(gt_ctx *c, int mode, int64_t trial_rays, int64_t trial_steps, double sp,
                 const char *cache_path, int *best_block, int *best_blocks_per_sm,
-                double *best_steps_per_s)
+                int *best_rays_per_thread, double *best_steps_per_s)
 {
     if (!c || trial_rays < 1 || trial_steps < 1 || !(sp > 0.0)) return GT_ERR_INVALID_ARG;
     if (mode != GT_MODE_FP64 && mode != GT_MODE_FP32_MIXED) return GT_ERR_INVALID_ARG;
@@ -937,25 +952,30 @@ int gt_autotune(gt_ctx *c, int mode, int64_t trial_rays, int64_t trial_steps, do
     if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess) return GT_ERR_CUDA;
     char key[256];
     snprintf(key, sizeof key, "mode=%d kind=%d sms=%d dev=%s", mode, kind, c->sm_count, prop.name);
+    auto report = [&](int b, int k, int rpt, double v) {
+        c->opts.block_size = b;
+        c->opts.blocks_per_sm = k;
+        c->opts.rays_per_thread = rpt;
+        if (best_block) *best_block = b;
+        if (best_blocks_per_sm) *best_blocks_per_sm = k;
+        if (best_rays_per_thread) *best_rays_per_thread = rpt;
+        if (best_steps_per_s) *best_steps_per_s = v;
+    };
     // cached result?
     if (cache_path) {
         FILE *f = fopen(cache_path, "r");
         if (f) {
             char line[512];
             while (fgets(line, sizeof line, f)) {
-                int b = 0, k = 0;
+                int b = 0, k = 0, rpt = 1;
                 double v = 0;
                 char *bar = strchr(line, '|');
                 if (!bar) continue;
                 *bar = 0;
-                if (strcmp(line, key) == 0 && sscanf(bar + 1, "%d %d %lf", &b, &k, &v) == 3 &&
-                    b >= 32 && b <= 256 && b % 32 == 0 && k >= 1 && k <= 64) {
+                if (strcmp(line, key) == 0 && sscanf(bar + 1, "%d %d %d %lf", &b, &k, &rpt, &v) == 4 &&
+                    b >= 32 && b <= 256 && b % 32 == 0 && k >= 1 && k <= 64 && (rpt == 1 || rpt == 2)) {
                     fclose(f);
-                    c->opts.block_size = b;
-                    c->opts.blocks_per_sm = k;
-                    if (best_block) *best_block = b;
-                    if (best_blocks_per_sm) *best_blocks_per_sm = k;
-                    if (best_steps_per_s) *best_steps_per_s = v;
+                    report(b, k, rpt, v);
                     return GT_OK;
                 }
             }
@@ -979,35 +999,41 @@ int gt_autotune(gt_ctx *c, int mode, int64_t trial_rays, int64_t trial_steps, do
     const gt_options saved = c->opts;
     const int blocks[] = {64, 128, 192, 256};
     const int per_sm[] = {1, 2, 3, 4, 6, 8};
-    int bb = 128, bk = 4;
+    const int n_rpt = mode == GT_MODE_FP32_MIXED ? 2 : 1;
+    int bb = 128, bk = 4, br = 1;
     double bv = -1.0;
     int rc = GT_OK;
-    for (int bi = 0; bi < 4 && rc == GT_OK; bi++) {
-        const int kmode = mode == GT_MODE_FP64 ? gt::KMODE_FP64 : gt::KMODE_MIXED_FP32;
-        const int fit = gt::max_blocks_per_sm(kmode, kind, blocks[bi]);
-        for (int ki = 0; ki < 6 && rc == GT_OK; ki++) {
-            if (per_sm[ki] > fit) continue;
-            c->opts = saved;
-            c->opts.block_size = blocks[bi];
-            c->opts.blocks_per_sm = per_sm[ki];
-            c->opts.timeout_seconds = 0.0;
-            double best_ms = 1e300;
-            for (int rep = 0; rep < 2 && rc == GT_OK; rep++) {
-                cudaEventRecord(e0, c->stream);
-                rc = gt_trace_range(c, first, count, trial_steps, sp, mode, buf, buf + count,
-                                    buf + 2 * count, buf + 3 * count, nullptr, ns);
-                cudaEventRecord(e1, c->stream);
-                if (cudaEventSynchronize(e1) != cudaSuccess) rc = GT_ERR_CUDA;
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (rep > 0 && ms < best_ms) best_ms = ms; // first run warms up
-            }
-            if (rc != GT_OK) break;
-            const double v = (double)count * (double)trial_steps / (best_ms * 1e-3);
-            if (v > bv) {
-                bv = v;
-                bb = blocks[bi];
-                bk = per_sm[ki];
+    for (int rpt = 1; rpt <= n_rpt && rc == GT_OK; rpt++) {
+        for (int bi = 0; bi < 4 && rc == GT_OK; bi++) {
+            const int kmode = mode == GT_MODE_FP64 ? gt::KMODE_FP64 : gt::KMODE_MIXED_FP32;
+            const int fit = rpt == 2 ? gt::max_blocks_per_sm_two(kind, blocks[bi])
+                                     : gt::max_blocks_per_sm(kmode, kind, blocks[bi]);
+            for (int ki = 0; ki < 6 && rc == GT_OK; ki++) {
+                if (per_sm[ki] > fit) continue;
+                c->opts = saved;
+                c->opts.block_size = blocks[bi];
+                c->opts.blocks_per_sm = per_sm[ki];
+                c->opts.rays_per_thread = rpt;
+                c->opts.timeout_seconds = 0.0;
+                double best_ms = 1e300;
+                for (int rep = 0; rep < 2 && rc == GT_OK; rep++) {
+                    cudaEventRecord(e0, c->stream);
+                    rc = gt_trace_range(c, first, count, trial_steps, sp, mode, buf, buf + count,
+                                        buf + 2 * count, buf + 3 * count, nullptr, ns);
+                    cudaEventRecord(e1, c->stream);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) rc = GT_ERR_CUDA;
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep > 0 && ms < best_ms) best_ms = ms; // first run warms up
+                }
+                if (rc != GT_OK) break;
+                const double v = (double)count * (double)trial_steps / (best_ms * 1e-3);
+                if (v > bv) {
+                    bv = v;
+                    bb = blocks[bi];
+                    bk = per_sm[ki];
+                    br = rpt;
+                }
             }
         }
     }
@@ -1017,15 +1043,11 @@ int gt_autotune(gt_ctx *c, int mode, int64_t trial_rays, int64_t trial_steps, do
     cudaFree(ns);
     c->opts = saved;
     if (rc != GT_OK) return rc;
-    c->opts.block_size = bb;
-    c->opts.blocks_per_sm = bk;
-    if (best_block) *best_block = bb;
-    if (best_blocks_per_sm) *best_blocks_per_sm = bk;
-    if (best_steps_per_s) *best_steps_per_s = bv;
+    report(bb, bk, br, bv);
     if (cache_path) {
         FILE *f = fopen(cache_path, "a");
         if (f) {
-            fprintf(f, "%s|%d %d %.6g\n", key, bb, bk, bv);
+            fprintf(f, "%s|%d %d %d %.6g\n", key, bb, bk, br, bv);
             fclose(f);
         }
     }
@@ -1037,6 +1059,20 @@ int gt_sync(gt_ctx *c)
     if (!c) return GT_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     return cuda_code(cudaStreamSynchronize(c->stream));
+}
+
+int gt_get_stats(gt_ctx *c, int64_t *zone_steps)
+{
+    if (!c || !zone_steps) return GT_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    if (!g.ok) return GT_ERR_CUDA;
+    unsigned long long v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, c->d_scratch + gt::SCR_ZONE_STEPS, sizeof v,
+                                    cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_code(e);
+    *zone_steps = (int64_t)v;
+    return GT_OK;
 }
 
 int gt_device_sm_count(gt_ctx *c, int *out)

@@ -39,7 +39,8 @@ enum : int {
     SCR_TIMEOUT = 1,    // set to 1 by the watchdog
     SCR_TO64 = 2,       // FP32-mixed: rays parked for the FP64 zone kernel
     SCR_TO32 = 3,       // FP32-mixed: rays handed back to the FP32 kernel
-    SCR_WORDS = 4
+    SCR_ZONE_STEPS = 4, // FP32-mixed: RK4 steps taken in the FP64 zone (gt_get_stats)
+    SCR_WORDS = 5
 };
 
 // Kernel modes (public GT_MODE_FP32_MIXED runs MIXED_FP32 and ZONE_FP64 in rounds).
@@ -162,5 +163,12 @@ cudaError_t launch_set_condition(cudaGraphConditionalHandle h, const unsigned lo
 int max_blocks_per_sm(int kmode, int kind_hint, int block);
 cudaError_t launch_trace(const TraceArgs &a, int kmode, int kind_hint, int block, int grid,
                          bool one_shot, cudaStream_t s);
+// The FP32 rounds kernel with two rays per thread (persistent launch only), when the
+// launch allows it (one camera of one spacetime kind; no watchdog, per-ray parameters,
+// state arrays or ring).
+bool two_rays_supported(const TraceArgs &a, int kmode, int kind_hint);
+cudaError_t launch_trace_two(const TraceArgs &a, int kind_hint, int block, int grid,
+                             cudaStream_t s);
+int max_blocks_per_sm_two(int kind_hint, int block);
 
 } // namespace gt

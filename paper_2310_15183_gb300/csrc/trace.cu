@@ -528,6 +528,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A, int one_shot)
     bool active = false;
     bool drained = false;
     uint32_t n = 0;
+    uint32_t n_entry = 0;           // step count when the ray entered this launch (zone steps)
     uint32_t rp_next = 0xFFFFFFFFu; // next step count that is a multiple of reproject_every
     Ray64 x;
     RayMixed m;
@@ -638,6 +639,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A, int one_shot)
             x.pt = it.pt;
             x.pph = it.pph;
         }
+        n_entry = n;
         if (MODE == 1 || MODE == 2) {
             mixed_from64(x, m);
             if (A.reproject_every > 0) {
@@ -749,7 +751,10 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A, int one_shot)
                 if (MODE == 3 && status < 0 && x.r > 1.25 * r_sw) { // leave the FP64 zone
                     bool ok;
                     park(A, id, n, cam, x, &ok);
-                    if (ok) active = false;
+                    if (ok) {
+                        active = false;
+                        atomicAdd(A.scratch + SCR_ZONE_STEPS, (unsigned long long)(n - n_entry));
+                    }
                 }
             }
         } else if (MODE == 1) {
@@ -838,6 +843,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A, int one_shot)
             if (status >= 0) mixed_to64(m, x);
         }
         if (status >= 0) {
+            if (MODE == 3) atomicAdd(A.scratch + SCR_ZONE_STEPS, (unsigned long long)(n - n_entry));
             double z = nan("");
             if (status == GT_RAY_DISK && A.z) z = redshift64<KIND>(cams[cam].st, cams[cam].gl_tt, x);
             store_full(A, id, x, status, n, z);
@@ -852,6 +858,177 @@ template <int MODE, int KIND, bool PRECISE = false>
 __global__ void __launch_bounds__(256, MODE == 2 ? 2 : 1) trace_kernel(TraceArgs A, int one_shot)
 {
     trace_body<MODE, KIND, PRECISE>(A, one_shot);
+}
+
+// ------------------------------------------------------------------ two rays per thread
+// The FP32 rounds kernel (MODE 2) with two independent ray slots per thread: both slots'
+// RK4 steps are issued back to back in one basic block, so the scheduler can interleave
+// two dependency chains (instruction-level parallelism at half the resident threads).
+// Same arithmetic per ray as trace_kernel<2, KIND>, so results are bitwise equal; for one
+// camera of a fixed spacetime kind, without the watchdog, per-ray parameters, state
+// arrays or the ring (the launcher falls back to one ray per thread otherwise).
+struct Slot32 {
+    bool active;
+    int64_t id;
+    uint32_t n, rp_next;
+    RayMixed m;
+};
+
+template <int KIND, bool PRECISE>
+__global__ void __launch_bounds__(256, 1) trace2_kernel(TraceArgs A)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    unsigned long long *next = A.scratch + SCR_NEXT_RAY;
+    const CamDesc &cam = A.cams[0];
+    const SpacetimeF stf = to_float(cam.st);
+    const F2 r_esc_f = f2_from(cam.r_escape);
+    const float r_sw_f = (float)cam.r_switch;
+    const float spf = A.sp_f, w6f = A.w6_f, h_thr_f = A.h_thr_f;
+    const int64_t n_in = A.in_count ? (int64_t)(*A.in_count < A.in_cap ? *A.in_count : A.in_cap) : 0;
+    const int64_t n_work = A.n_fresh + n_in;
+    Slot32 sl[2];
+    sl[0].active = sl[1].active = false;
+    bool drained = false;
+    Ray64 x;
+
+    auto start = [&](Slot32 &q, int64_t w) {
+        if (w < A.n_fresh) {
+            const int64_t pix = A.fresh_ids ? A.fresh_ids[w] : w;
+            q.id = (A.fresh_ids && A.compact_out) ? w : pix;
+            camera_init(cam, A.first + pix, x);
+            q.n = 0;
+            if (A.n_steps <= 0) {
+                store_full(A, q.id, x, GT_RAY_MAXSTEPS, 0, nan(""));
+                return false;
+            }
+        } else {
+            const ParkItem &it = A.in_items[w - A.n_fresh];
+            q.id = it.id;
+            q.n = it.n;
+            x.t = it.t;
+            x.r = it.r;
+            x.th = it.th;
+            x.ph = it.ph;
+            x.pr = it.pr;
+            x.pth = it.pth;
+            x.pt = it.pt;
+            x.pph = it.pph;
+        }
+        mixed_from64(x, q.m);
+        q.rp_next = 0xFFFFFFFFu;
+        if (A.reproject_every > 0) {
+            const uint64_t k = (uint64_t)A.reproject_every;
+            const uint64_t nx = ((uint64_t)q.n / k + 1u) * k;
+            q.rp_next = nx < 0xFFFFFFFFull ? (uint32_t)nx : 0xFFFFFFFFu;
+        }
+        return true;
+    };
+
+    // exit tests, zone hand-over and re-projection of one slot after its step
+    auto finish = [&](Slot32 &q, float h, const RayMixed &keep) {
+        ++q.n;
+        int status = -1;
+        const bool ok = isfinite(h) && isfinite(q.m.t.hi) && isfinite(q.m.r.hi) &&
+                        isfinite(q.m.th.hi) && isfinite(q.m.ph.hi) && isfinite(q.m.pr.hi) &&
+                        isfinite(q.m.pth.hi);
+        if (!ok) {
+            q.m = keep;
+            status = GT_RAY_NONFINITE;
+        } else if (q.m.r.hi > r_esc_f.hi || (q.m.r.hi == r_esc_f.hi && q.m.r.lo > r_esc_f.lo)) {
+            status = GT_RAY_ESCAPED;
+        } else if (h < h_thr_f) {
+            status = GT_RAY_HORIZON;
+        } else if ((int64_t)q.n >= A.n_steps) {
+            status = GT_RAY_MAXSTEPS;
+        } else if (q.m.r.hi < r_sw_f) { // enter the FP64 zone: hand the ray over
+            mixed_to64(q.m, x);
+            bool parked;
+            park(A, q.id, q.n, 0, x, &parked);
+            if (parked) q.active = false;
+        } else if (q.n == q.rp_next) {
+            q.rp_next = q.rp_next + (uint32_t)A.reproject_every < q.rp_next
+                            ? 0xFFFFFFFFu
+                            : q.rp_next + (uint32_t)A.reproject_every;
+            mixed_to64(q.m, x);
+            reproject_pr(cam.st, x);
+            q.m.pr = f2_from(x.pr);
+        }
+        if (status >= 0) {
+            mixed_to64(q.m, x);
+            store_full(A, q.id, x, status, q.n, nan(""));
+            q.active = false;
+        }
+    };
+
+    for (;;) {
+#pragma unroll
+        for (int k = 0; k < 2; k++) { // refill each slot from the global queue
+            if (drained) break;
+            const unsigned need = __ballot_sync(FULL_MASK, !sl[k].active);
+            if (need) {
+                const int cnt = __popc(need);
+                const int leader = __ffs(need) - 1;
+                unsigned long long base = 0;
+                if (lane == leader) base = atomicAdd(next, (unsigned long long)cnt);
+                base = __shfl_sync(FULL_MASK, base, leader);
+                if (base + (unsigned long long)cnt >= (unsigned long long)n_work) drained = true;
+                if (!sl[k].active) {
+                    const int64_t w = (int64_t)base + __popc(need & lt_mask);
+                    if (w < n_work) sl[k].active = start(sl[k], w);
+                }
+            }
+        }
+        if (!__any_sync(FULL_MASK, sl[0].active || sl[1].active)) {
+            if (drained) break;
+            continue;
+        }
+        // both steps back to back (an idle slot steps its last state; the result is unused)
+        const RayMixed keep0 = sl[0].m, keep1 = sl[1].m;
+        const float h0 = rk4_step32<KIND, PRECISE>(stf, sl[0].m, spf, w6f);
+        const float h1 = rk4_step32<KIND, PRECISE>(stf, sl[1].m, spf, w6f);
+        if (sl[0].active) finish(sl[0], h0, keep0);
+        if (sl[1].active) finish(sl[1], h1, keep1);
+    }
+}
+
+template <int KIND>
+static cudaError_t launch_two(const TraceArgs &a, int block, int grid, cudaStream_t s)
+{
+    if constexpr (KIND == KIND_MN) {
+        if (a.flags & GT_FLAG_PRECISE_MN) {
+            trace2_kernel<KIND, true><<<grid, block, 0, s>>>(a);
+            return cudaGetLastError();
+        }
+    }
+    trace2_kernel<KIND, false><<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+bool two_rays_supported(const TraceArgs &a, int kmode, int kind_hint)
+{
+    return kmode == KMODE_MIXED_FP32 && (kind_hint == KIND_KERR || kind_hint == KIND_MN) &&
+           a.n_cams == 1 && !a.rays && !a.states.t && !a.disk.on && a.timeout_ns == 0;
+}
+
+cudaError_t launch_trace_two(const TraceArgs &args, int kind_hint, int block, int grid,
+                             cudaStream_t s)
+{
+    TraceArgs a = args;
+    a.sp_f = (float)a.sp;
+    a.w6_f = (float)a.w6;
+    a.h_thr_f = (float)(a.sp * 0.00003);
+    return kind_hint == KIND_KERR ? launch_two<KIND_KERR>(a, block, grid, s)
+                                  : launch_two<KIND_MN>(a, block, grid, s);
+}
+
+int max_blocks_per_sm_two(int kind_hint, int block)
+{
+    int n = 0;
+    const cudaError_t e = kind_hint == KIND_KERR
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, trace2_kernel<KIND_KERR, false>, block, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, trace2_kernel<KIND_MN, false>, block, 0);
+    return (e == cudaSuccess && n > 0) ? n : 1;
 }
 
 // Loop condition of the graph-resident FP32-mixed rounds: continue while rays are parked.

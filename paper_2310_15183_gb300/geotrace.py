@@ -33,7 +33,8 @@ EXPORTS = ("gt_create", "gt_destroy", "gt_set_stream", "gt_set_spacetime", "gt_s
            "gt_trace_rays", "gt_autotune", "gt_surrogate_num_params", "gt_surrogate_create",
            "gt_surrogate_destroy", "gt_surrogate_get_params", "gt_surrogate_set_params",
            "gt_surrogate_eval", "gt_surrogate_grad", "gt_surrogate_train", "gt_surrogate_infer",
-           "gt_trace_disk", "gt_trace_states", "gt_surrogate_get_grads", "gt_strerror")
+           "gt_trace_disk", "gt_trace_states", "gt_surrogate_get_grads", "gt_get_stats",
+           "gt_strerror")
 
 
 class GeotraceError(RuntimeError):
@@ -45,7 +46,8 @@ class GeotraceError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("block_size", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
                 ("flags", ctypes.c_int), ("reproject_every", ctypes.c_int),
-                ("r_switch", ctypes.c_double), ("timeout_seconds", ctypes.c_double)]
+                ("r_switch", ctypes.c_double), ("timeout_seconds", ctypes.c_double),
+                ("rays_per_thread", ctypes.c_int)]
 
 
 class SurrogateNorm(ctypes.Structure):
@@ -95,12 +97,13 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.gt_trace_batch.argtypes = [vp, ctypes.POINTER(CameraDesc), i, i64, d, i] + out6
     lib.gt_sync.argtypes = [vp]
     lib.gt_device_sm_count.argtypes = [vp, ctypes.POINTER(i)]
+    lib.gt_get_stats.argtypes = [vp, ctypes.POINTER(i64)]
     lib.gt_measure_fma_peak.argtypes = [i, i, i, ctypes.POINTER(d)]
     lib.gt_gemm_bf16.argtypes = [i, vp, i, i, i, vp, i64, i64, vp, i64, i64, vp, i, vp, i64,
                                  i, i, i]
     lib.gt_trace_batch_noalloc.argtypes = [i, vp, ctypes.POINTER(CameraDesc), i, i64, d, i] + out6
     lib.gt_autotune.argtypes = [vp, i, i64, i64, d, ctypes.c_char_p, ctypes.POINTER(i),
-                                ctypes.POINTER(i), ctypes.POINTER(d)]
+                                ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(d)]
     lib.gt_trace_rays.argtypes = [vp, i64] + [vp] * 5 + [d, d, i64, d, i] + out6
     lib.gt_surrogate_num_params.argtypes = [ctypes.POINTER(i64)]
     lib.gt_surrogate_create.argtypes = [i, ctypes.POINTER(SurrogateNorm), ctypes.c_uint64,
@@ -173,6 +176,12 @@ class Tracer:
         except Exception:
             pass
 
+    def zone_steps(self) -> int:
+        """RK4 steps the last trace took in the FP64 zone (gt_get_stats)."""
+        v = ctypes.c_int64()
+        _check(self.lib.gt_get_stats(self.ctx, ctypes.byref(v)), "gt_get_stats")
+        return v.value
+
     def sm_count(self) -> int:
         n = ctypes.c_int()
         _check(self.lib.gt_device_sm_count(self.ctx, ctypes.byref(n)), "gt_device_sm_count")
@@ -187,8 +196,9 @@ class Tracer:
         self.res = (res_x, res_y)
 
     def set_options(self, block_size=0, blocks_per_sm=0, flags=0, reproject_every=0,
-                    r_switch=0.0, timeout_seconds=0.0):
-        o = Options(block_size, blocks_per_sm, flags, reproject_every, r_switch, timeout_seconds)
+                    r_switch=0.0, timeout_seconds=0.0, rays_per_thread=0):
+        o = Options(block_size, blocks_per_sm, flags, reproject_every, r_switch, timeout_seconds,
+                    rays_per_thread)
         _check(self.lib.gt_set_options(self.ctx, ctypes.byref(o)), "gt_set_options")
 
     def alloc_outputs(self, n: int) -> dict:
@@ -303,14 +313,16 @@ class Tracer:
 
     def autotune(self, mode: int, trial_rays: int = 1 << 17, trial_steps: int = 400,
                  step_precision: float = 1.5e-4, cache_path: Optional[str] = None):
-        """gt_autotune: returns (block_size, blocks_per_sm, trial steps/s) and keeps them."""
-        b, k, v = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        """gt_autotune: returns (block_size, blocks_per_sm, rays_per_thread, trial steps/s)
+        and keeps them in the context's options."""
+        b, k, rpt, v = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
         _check(self.lib.gt_autotune(self.ctx, int(mode), int(trial_rays), int(trial_steps),
                                     float(step_precision),
                                     cache_path.encode() if cache_path else None,
-                                    ctypes.byref(b), ctypes.byref(k), ctypes.byref(v)),
+                                    ctypes.byref(b), ctypes.byref(k), ctypes.byref(rpt),
+                                    ctypes.byref(v)),
                "gt_autotune")
-        return b.value, k.value, v.value
+        return b.value, k.value, rpt.value, v.value
 
     def trace_rays(self, alpha, beta, spin, q, theta0, M: float, r0: float, n_steps: int,
                    step_precision: float, mode: int = MODE_FP32_MIXED,

@@ -316,15 +316,35 @@ def test_autotuner_picks_valid_shape_caches_it_and_keeps_bits(g, tracer, tmp_pat
     cam = W.sub_camera(MN, 96, 64)
     base = run_gpu(tracer, cam, 2500, 1.5e-4, mode=0)
     cache = str(tmp_path / "tune.txt")
-    b, k, v = tracer.autotune(0, trial_rays=4096, trial_steps=200, cache_path=cache)
-    assert b in (64, 128, 192, 256) and 1 <= k <= 8 and v > 0
+    b, k, rpt, v = tracer.autotune(0, trial_rays=4096, trial_steps=200, cache_path=cache)
+    assert b in (64, 128, 192, 256) and 1 <= k <= 8 and rpt == 1 and v > 0
     assert open(cache).read().count("|") == 1
-    b2, k2, v2 = tracer.autotune(0, trial_rays=4096, trial_steps=200, cache_path=cache)
-    assert (b2, k2) == (b, k)
+    b2, k2, rpt2, v2 = tracer.autotune(0, trial_rays=4096, trial_steps=200, cache_path=cache)
+    assert (b2, k2, rpt2) == (b, k, rpt)
     out = to_numpy(tracer.trace(2500, 1.5e-4, 0))  # tuned shape kept in the context
     torch.cuda.synchronize()
     for key in ("t", "r", "th", "ph", "status", "nsteps"):
         assert np.array_equal(out[key], base[key]), key
+
+
+def test_two_rays_per_thread_is_bitwise_equal_and_tuned(g, tracer, tmp_path):
+    """The FP32 rounds kernel with two rays per thread runs the same arithmetic per ray:
+    bitwise equal to one ray per thread, for the literal workload and for terminating rays
+    that park in and return from an FP64 zone; the autotuner searches it for FP32-mixed."""
+    for cam, n_steps, rsw in ((W.sub_camera(MN, 24, 16), 20000, 0.0),
+                              (KERR, 300000, 1.5), (W.sub_camera(MN, 10, 8), 300000, 0.0)):
+        one = run_gpu(tracer, cam, n_steps, 1.5e-4, mode=1, r_switch=rsw)
+        two = run_gpu(tracer, cam, n_steps, 1.5e-4, mode=1, r_switch=rsw, rays_per_thread=2)
+        for k in ("t", "r", "th", "ph", "status", "nsteps"):
+            assert np.array_equal(one[k], two[k]), (cam, k)
+    cam = W.sub_camera(MN, 96, 64)
+    tracer.set_spacetime(cam.M, cam.S, cam.Q)
+    tracer.set_camera(cam.r0, cam.theta0, cam.fov_deg, cam.res_x, cam.res_y)
+    tracer.set_options()
+    b, k, rpt, v = tracer.autotune(1, trial_rays=4096, trial_steps=200,
+                                   cache_path=str(tmp_path / "tune1.txt"))
+    assert rpt in (1, 2) and v > 0
+    assert open(str(tmp_path / "tune1.txt")).read().split("|")[1].split()[2] == str(rpt)
 
 
 def test_graph_launch_replays_the_batch(g, tracer, oracle):
@@ -450,3 +470,24 @@ def test_overflowing_step_is_nonfinite_and_keeps_the_camera_state(tracer, oracle
         assert np.array_equal(got["nsteps"], ref["nsteps"])
         for k in ("t", "r", "th", "ph"):
             assert np.max(np.abs(got[k] - ref[k])) <= 1e-15 * max(1.0, np.max(np.abs(ref[k]))), k
+
+
+# ----------------------------------------------------------------- Manko-Novikov zoo
+ZOO = [(q, S) for q in (-2.0, 0.0, 2.0) for S in (0.1 * 0.25, 0.98 * 0.25)]
+
+
+@pytest.mark.parametrize("q,S", ZOO)
+def test_fp64_mn_zoo(tracer, oracle, q, S):
+    """The spacetimes of the paper's shadow zoo (q in {-2, 0, 2} x S in {0.1M^2, 0.98M^2};
+    q = 0 is Kerr): FP64 against the oracle on a 10x8 image from the listing's viewpoint
+    r0 = 16M, 80 deg, FOV 60 deg, to a 250,000-step cap (rays escape, fall in or stay
+    trapped), outside the chaotic boundary band and axis crossings; then FP32-mixed with
+    the same classification and 1e-3 rad."""
+    cam = W.Camera(M=0.5, S=S, Q=q, r0=8.0, theta0=80 * W.DEG, fov_deg=60.0, res_x=10, res_y=8)
+    got = run_gpu(tracer, cam, 250000, 1.5e-4)
+    ref = run_oracle(oracle, cam, 250000, 1.5e-4, want_min_sin=True)
+    band = neighbour_band(ref["status"], cam.res_x, cam.res_y) | (ref["min_sin"] < 1e-3)
+    assert_fp64_parity(got, ref, exclude=band, what=f"zoo q={q} S={S}")
+    mixed = run_gpu(tracer, cam, 250000, 1.5e-4, mode=1)
+    rep = mixed_report(mixed, ref, exclude=band)
+    assert rep["agree"] >= 0.999 and rep["max_angle_escaped"] <= 1e-3, rep

@@ -566,7 +566,8 @@ def mode_surrogate(tr, geotrace, torch, args) -> dict:
     """Surrogate + fallback at a reduced training budget: label sg_default_rays rays with the
     integrator (FP32-mixed, 500,000-step cap) over the training ranges at r0 = 30M, train,
     then image a Kerr a = 0.9M, 80 deg camera of sg_default_res^2 pixels with integrator
-    probes every 8 pixels (tolerance 1e-3) and fallback; against integrator-only on the same
+    probes every 8 pixels (tolerance 1e-3), the photon-ring and axis gates (0.02) and
+    fallback; against integrator-only on the same
     image (time) and the FP64 integrator on a pixel sample of the network's pixels (error)."""
     import numpy as np
     M, r0, sp, cap = 0.5, 15.0, 1.5e-4, 500000
@@ -589,8 +590,8 @@ def mode_surrogate(tr, geotrace, torch, args) -> dict:
     full = tr.trace(cap, sp, geotrace.MODE_FP32_MIXED)  # warm
     full, t_full = _timed(torch, tr.stream, lambda: tr.trace(cap, sp, geotrace.MODE_FP32_MIXED))
     out = tr.alloc_outputs(cam.n_rays)
-    infer = lambda: sg.infer(tr, 2.0, 0.0, cap, sp, geotrace.MODE_FP32_MIXED, out=out,
-                             probe_stride=8, probe_tol=1e-3, with_probes=True)
+    infer = lambda: sg.infer(tr, 2.0, 0.02, cap, sp, geotrace.MODE_FP32_MIXED, out=out,
+                             probe_stride=8, probe_tol=1e-3, axis=0.02, with_probes=True)
     infer()
     (out, nfb, npr), t_inf = _timed(torch, tr.stream, infer)
     ns = out["nsteps"].cpu().numpy().view(np.uint32)
@@ -617,7 +618,8 @@ def mode_surrogate(tr, geotrace, torch, args) -> dict:
             "integrator_only_seconds": t_full, "speedup_vs_integrator_only": t_full / t_inf,
             "probe_pixels": npr, "fallback_pixels": nfb,
             "network_pixel_fraction": net.size / cam.n_rays,
-            "gates": {"tau": 2.0, "probe_stride": 8, "probe_tol": 1e-3},
+            "gates": {"tau": 2.0, "band": 0.02, "axis": 0.02, "probe_stride": 8,
+                      "probe_tol": 1e-3},
             "accuracy_vs_fp64": acc, "network_alone_vs_fp64": acc_raw,
             "judge": f"FP64 integrator on {judge.size} seeded network pixels"}
 

@@ -277,8 +277,23 @@ int gt_surrogate_train(gt_ctx *ctx, gt_surrogate *s, const gt_train_cfg *cfg, in
                        const double *q, const double *theta0, const uint8_t *status,
                        const double *th_end, const double *ph_end, float *loss_per_epoch);
 
+/* Gates of gt_surrogate_infer (zero fields disable a gate). */
+typedef struct gt_gate_cfg {
+    float tau;         /* network pixels need |logit| >= tau */
+    double band;       /* Kerr photon-ring band: |min_r R(r)/(E^2 r^4)| < band falls back
+                          (97 geometric radii from 1.0001 r_+ to r0, from the pixel's
+                          constants of motion) */
+    double axis;       /* rays that can reach |sin theta| < axis fall back (Kerr turning
+                          point of the theta motion from the pixel's constants of motion;
+                          the Kerr values of M and S estimate it for Manko-Novikov); in [0, 1) */
+    float dir_tol;     /* escaping predictions whose direction vector's length is off 1 by
+                          more than dir_tol fall back */
+    int probe_stride;  /* integrator probes every probe_stride pixels (0 = none) */
+    float probe_tol;   /* largest accepted spread of the probe errors over a cell */
+} gt_gate_cfg;
+
 /* Image of the configured camera through the surrogate, with the integrator as judge and
- * fallback.  With probe_stride > 0 the integrator first traces the probe pixels
+ * fallback.  With gate->probe_stride > 0 the integrator first traces the probe pixels
  * (i, j) with i, j multiples of probe_stride or the last column/row (images of at least
  * 2 x 2 pixels); their exact results go to the image, and each probe records the
  * network's error vector (exact unit end direction minus the predicted one).  A pixel
@@ -286,20 +301,15 @@ int gt_surrogate_train(gt_ctx *ctx, gt_surrogate *s, const gt_train_cfg *cfg, in
  * are classified alike by the integrator and the network -- all escaped, or all HORIZON
  * -- and, when escaping, the corners' error vectors differ by less than probe_tol
  * (|e00 - e11| and |e01 - e10|); its end direction is the network's plus the bilinear
- * interpolation of the corner errors.  In every case a pixel also needs |logit| >= tau,
- * lies outside the Kerr photon-ring band (|min_r R(r)/(E^2 r^4)| < band over 97
- * geometric radii from 1.0001 r_+ to r0, from the pixel's constants of motion;
- * band = 0 disables) and, when predicted to escape, has a predicted direction vector of
- * length within dir_tol of 1 (dir_tol = 0 disables).  Network pixels get status
- * ESCAPED with end theta, phi from the (corrected) direction, or HORIZON with NaN
- * angles; t and r are NaN and nsteps 0 for them.  All other pixels are traced by the
- * integrator (mode, n_steps, step_precision as gt_trace) and written in place.  Outputs
- * as gt_trace (device, res_x*res_y each, none may be NULL); *n_fallback receives the
- * number of integrated pixels besides the probes, *n_probes the number of probes (either
- * may be NULL).  Errors: GT_ERR_INVALID_ARG (negative tau, band, dir_tol, probe_stride or
- * probe_tol, NULL outputs) and those of gt_trace.  Synchronous. */
-int gt_surrogate_infer(gt_ctx *ctx, gt_surrogate *s, float tau, double band, float dir_tol,
-                       int probe_stride, float probe_tol, int64_t n_steps,
+ * interpolation of the corner errors.  In every case a network pixel also passes the
+ * gates of gt_gate_cfg.  Network pixels get status ESCAPED with end theta, phi from the
+ * (corrected) direction, or HORIZON with NaN angles; t and r are NaN and nsteps 0 for
+ * them.  All other pixels are traced by the integrator (mode, n_steps, step_precision as
+ * gt_trace) and written in place.  Outputs as gt_trace (device, res_x*res_y each, none may
+ * be NULL); *n_fallback receives the number of integrated pixels besides the probes,
+ * *n_probes the number of probes (either may be NULL).  Errors: GT_ERR_INVALID_ARG (gate
+ * NULL or out of range, NULL outputs) and those of gt_trace.  Synchronous. */
+int gt_surrogate_infer(gt_ctx *ctx, gt_surrogate *s, const gt_gate_cfg *gate, int64_t n_steps,
                        double step_precision, int mode, double *t, double *r, double *theta,
                        double *phi, uint8_t *status, uint32_t *nsteps, int64_t *n_fallback,
                        int64_t *n_probes);

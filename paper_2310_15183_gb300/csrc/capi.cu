@@ -66,7 +66,7 @@ cudaStream_t gt_internal_stream(gt_ctx *c) { return c->stream; }
 namespace gt {
 namespace sg {
 int infer_chunks(gt_surrogate *s, const CamDesc *d_cam, int64_t n_pix, float tau, double band,
-                 float dir_tol, const ProbeGrid &pg, double *t, double *r, double *th, double *ph,
+                 double axis, float dir_tol, const ProbeGrid &pg, double *t, double *r, double *th, double *ph,
                  uint8_t *status, uint32_t *nsteps, int64_t *d_fallback, unsigned long long *d_nfb,
                  cudaStream_t st);
 int probe_pixels(const CamDesc *d_cam, const ProbeGrid &pg, int64_t *d_pix, cudaStream_t st);
@@ -857,15 +857,18 @@ int gt_trace_rays(gt_ctx *c, int64_t n, const double *alpha, const double *beta,
                      nullptr, c->d_rays);
 }
 
-int gt_surrogate_infer(gt_ctx *c, gt_surrogate *s, float tau, double band, float dir_tol,
-                       int probe_stride, float probe_tol, int64_t n_steps, double sp, int mode,
-                       double *t, double *r, double *th, double *ph, uint8_t *status,
-                       uint32_t *nsteps, int64_t *n_fallback, int64_t *n_probes)
+int gt_surrogate_infer(gt_ctx *c, gt_surrogate *s, const gt_gate_cfg *gate, int64_t n_steps,
+                       double sp, int mode, double *t, double *r, double *th, double *ph,
+                       uint8_t *status, uint32_t *nsteps, int64_t *n_fallback, int64_t *n_probes)
 {
     int rc = check_common(c, n_steps, sp, mode);
     if (rc != GT_OK) return rc;
-    if (!s || !t || !r || !th || !ph || !status || !nsteps || !(tau >= 0.0f) || !(band >= 0.0) ||
-        !(dir_tol >= 0.0f) || probe_stride < 0 || !(probe_tol >= 0.0f))
+    if (!s || !gate || !t || !r || !th || !ph || !status || !nsteps) return GT_ERR_INVALID_ARG;
+    const float tau = gate->tau, dir_tol = gate->dir_tol, probe_tol = gate->probe_tol;
+    const double band = gate->band, axis = gate->axis;
+    const int probe_stride = gate->probe_stride;
+    if (!(tau >= 0.0f) || !(band >= 0.0) || !(axis >= 0.0 && axis < 1.0) || !(dir_tol >= 0.0f) ||
+        probe_stride < 0 || !(probe_tol >= 0.0f))
         return GT_ERR_INVALID_ARG;
     if (!c->st_set || !c->cam_set) return GT_ERR_NOT_CONFIGURED;
     if (!aligned8(t) || !aligned8(r) || !aligned8(th) || !aligned8(ph) || ((uintptr_t)nsteps & 3u))
@@ -925,8 +928,8 @@ int gt_surrogate_infer(gt_ctx *c, gt_surrogate *s, float tau, double band, float
     unsigned long long *d_nfb = c->d_scratch + gt::SCR_TO32; // free until the fallback trace
     cudaError_t err = cudaMemsetAsync(d_nfb, 0, sizeof(unsigned long long), c->stream);
     if (err != cudaSuccess) return cuda_code(err);
-    rc = gt::sg::infer_chunks(s, c->d_cam, n_pix, tau, band, dir_tol, pg, t, r, th, ph, status,
-                              nsteps, c->d_fallback, d_nfb, c->stream);
+    rc = gt::sg::infer_chunks(s, c->d_cam, n_pix, tau, band, axis, dir_tol, pg, t, r, th, ph,
+                              status, nsteps, c->d_fallback, d_nfb, c->stream);
     if (rc != GT_OK) return rc;
     unsigned long long nfb = 0;
     err = cudaMemcpyAsync(&nfb, d_nfb, sizeof nfb, cudaMemcpyDeviceToHost, c->stream);

@@ -250,18 +250,29 @@ __global__ void weights_split_kernel(const float *W, int out_dim, int in_dim, __
     row[2 * in_dim + i] = lo;
 }
 
-// Photon-ring test for a Kerr pixel: with E = -p_t, L = p_phi and the Carter constant
-// K of the initial momentum, the radial potential
-//   R(r) = (E (r^2 + a^2) - a L)^2 - Delta ((L - a E)^2 + K)
+// Constants of motion of a camera ray in the Kerr picture: E = -p_t, L = p_phi and the
+// Carter constant K = p_theta^2 + cos^2 theta0 (-a^2 E^2 + L^2/sin^2 theta0), with a = S/M
+// (Manko-Novikov rays take the Kerr values of their M and S: an estimate there).
+__device__ __forceinline__ void kerr_constants(const CamDesc &c, const Ray64 &p, double *a,
+                                               double *E, double *L, double *K)
+{
+    *a = c.S / c.M;
+    *E = -p.pt;
+    *L = p.pph;
+    const double ct = cos(c.th0), st = sin(c.th0);
+    *K = p.pth * p.pth + ct * ct * (-(*a) * (*a) * (*E) * (*E) + (*L) * (*L) / (st * st));
+}
+
+// Photon-ring test for a Kerr pixel: the radial potential of its constants of motion,
+//   R(r) = (E (r^2 + a^2) - a L)^2 - Delta ((L - a E)^2 + K),
 // has a (near) double root for rays near the critical curve.  Returns
 // min over r in (r_+, r0] of R(r) / (E^2 r^4) on a geometric grid.
 __device__ double kerr_rmin(const CamDesc &c, const Ray64 &p)
 {
-    const double a = c.st.a, M = c.M;
-    const double E = -p.pt, L = p.pph;
-    const double ct = cos(c.th0), st = sin(c.th0);
-    const double K = p.pth * p.pth + ct * ct * (-a * a * E * E + L * L / (st * st));
-    const double rp = c.st.r_plus;
+    double a, E, L, K;
+    kerr_constants(c, p, &a, &E, &L, &K);
+    const double M = c.M;
+    const double rp = c.st.kind == KIND_KERR ? c.st.r_plus : M + sqrt(fmax(M * M - a * a, 0.0));
     const double lo = log(rp * 1.0001), hi = log(c.r0);
     double best = 1e300;
     for (int k = 0; k <= 96; k++) {
@@ -273,6 +284,29 @@ __device__ double kerr_rmin(const CamDesc &c, const Ray64 &p)
         best = v < best ? v : best;
     }
     return best;
+}
+
+// Smallest sin^2 theta a Kerr ray can reach: the theta potential
+// Theta = K + a^2 E^2 cos^2 - L^2 cot^2 vanishes at u = cos^2 theta solving
+// -a^2 E^2 u^2 + (a^2 E^2 - K - L^2) u + K = 0; returns 1 - u for its root in [0, 1].
+// Rays that pass close to the axis sweep phi fast and end in directions that change
+// abruptly from pixel to pixel.
+__device__ double kerr_min_sin2(const CamDesc &c, const Ray64 &p)
+{
+    double a, E, L, K;
+    kerr_constants(c, p, &a, &E, &L, &K);
+    const double A = -a * a * E * E, B = a * a * E * E - K - L * L, C = K;
+    double u;
+    if (fabs(A) < 1e-300) {
+        u = (K + L * L) > 0.0 ? K / (K + L * L) : 0.0;
+    } else {
+        const double disc = sqrt(fmax(B * B - 4.0 * A * C, 0.0));
+        const double u1 = (-B + disc) / (2.0 * A), u2 = (-B - disc) / (2.0 * A);
+        u = 0.0;
+        if (u1 >= 0.0 && u1 <= 1.0) u = fmax(u, u1);
+        if (u2 >= 0.0 && u2 <= 1.0) u = fmax(u, u2);
+    }
+    return 1.0 - u;
 }
 
 // Probe pixel columns: k stride for k < n - 1, and the last column (res - 1).
@@ -342,7 +376,7 @@ __global__ void scatter_probes_kernel(int n, const int64_t *pix, const double *p
 // pg.tol; its end direction is the network's plus the bilinear interpolation of the
 // corners' error vectors (the integrator correcting the network where it measured it).
 __global__ void gate_kernel(int64_t n, int64_t pix0, const CamDesc *cam, const float *Z5, float tau,
-                            double band, float dir_tol, ProbeGrid pg, double *t, double *r,
+                            double band, double axis, float dir_tol, ProbeGrid pg, double *t, double *r,
                             double *th, double *ph, uint8_t *status, uint32_t *nsteps,
                             int64_t *fallback, unsigned long long *n_fallback)
 {
@@ -400,10 +434,11 @@ __global__ void gate_kernel(int64_t n, int64_t pix0, const CamDesc *cam, const f
         }
         if (!skip && !fb) {
             bool ring = false;
-            if (band > 0.0 && cam->st.kind == KIND_KERR) {
+            if ((band > 0.0 && cam->st.kind == KIND_KERR) || axis > 0.0) {
                 Ray64 p;
                 camera_init(*cam, pix, p);
-                ring = fabs(kerr_rmin(*cam, p)) < band;
+                if (band > 0.0 && cam->st.kind == KIND_KERR) ring = fabs(kerr_rmin(*cam, p)) < band;
+                if (axis > 0.0) ring = ring || kerr_min_sin2(*cam, p) < axis * axis;
             }
             const float nn = sqrtf(z[1] * z[1] + z[2] * z[2] + z[3] * z[3]);
             // an escaping prediction whose direction vector is not of unit length is unsettled
@@ -901,7 +936,7 @@ namespace gt {
 namespace sg {
 
 int infer_chunks(gt_surrogate *s, const CamDesc *d_cam, int64_t n_pix, float tau, double band,
-                 float dir_tol, const ProbeGrid &pg, double *t, double *r, double *th, double *ph,
+                 double axis, float dir_tol, const ProbeGrid &pg, double *t, double *r, double *th, double *ph,
                  uint8_t *status, uint32_t *nsteps, int64_t *d_fallback, unsigned long long *d_nfb,
                  cudaStream_t st)
 {
@@ -914,7 +949,7 @@ int infer_chunks(gt_surrogate *s, const CamDesc *d_cam, int64_t n_pix, float tau
         cudaError_t e = forward(s, (int)B, st, false);
         if (e != cudaSuccess) return GT_ERR_CUDA;
         gate_kernel<<<blocks_for(B), 256, 0, st>>>(B, p0, d_cam, s->Z[N_LAYERS - 1], tau, band,
-                                                   dir_tol, pg, t, r, th, ph, status, nsteps,
+                                                   axis, dir_tol, pg, t, r, th, ph, status, nsteps,
                                                    d_fallback, d_nfb);
         if (cudaGetLastError() != cudaSuccess) return GT_ERR_CUDA;
     }

@@ -61,6 +61,12 @@ class TrainCfg(ctypes.Structure):
                 ("weight_decay", ctypes.c_double), ("dir_weight", ctypes.c_double)]
 
 
+class GateCfg(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_float), ("band", ctypes.c_double), ("axis", ctypes.c_double),
+                ("dir_tol", ctypes.c_float), ("probe_stride", ctypes.c_int),
+                ("probe_tol", ctypes.c_float)]
+
+
 class CameraDesc(ctypes.Structure):
     _fields_ = [("M", ctypes.c_double), ("S", ctypes.c_double), ("Q", ctypes.c_double),
                 ("r0", ctypes.c_double), ("theta0", ctypes.c_double),
@@ -114,8 +120,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.gt_surrogate_eval.argtypes = [vp, vp, i64] + [vp] * 5 + [vp]
     lib.gt_surrogate_grad.argtypes = [vp, vp, i64] + [vp] * 8 + [ctypes.c_float, vp, vp]
     lib.gt_surrogate_train.argtypes = [vp, vp, ctypes.POINTER(TrainCfg), i64] + [vp] * 8 + [vp]
-    lib.gt_surrogate_infer.argtypes = [vp, vp, ctypes.c_float, d, ctypes.c_float, i,
-                                       ctypes.c_float, i64, d, i] + out6 + [
+    lib.gt_surrogate_infer.argtypes = [vp, vp, ctypes.POINTER(GateCfg), i64, d, i] + out6 + [
         ctypes.POINTER(i64), ctypes.POINTER(i64)]
     lib.gt_surrogate_get_grads.argtypes = [vp, vp, i64]
     lib.gt_strerror.argtypes = [i]
@@ -417,15 +422,16 @@ class Surrogate:
     def infer(self, tracer: "Tracer", tau: float, band: float, n_steps: int,
               step_precision: float, mode: int = MODE_FP32_MIXED, out: Optional[dict] = None,
               dir_tol: float = 0.0, probe_stride: int = 0, probe_tol: float = 0.0,
-              with_probes: bool = False):
+              axis: float = 0.0, with_probes: bool = False):
         """gt_surrogate_infer; returns (outputs, integrated pixels besides the probes) or,
         with with_probes, (outputs, fallback pixels, probe pixels)."""
         n = tracer.res[0] * tracer.res[1]
         if out is None:
             out = tracer.alloc_outputs(n)
         nfb, npr = ctypes.c_int64(), ctypes.c_int64()
-        _check(self.lib.gt_surrogate_infer(tracer.ctx, self.h, float(tau), float(band),
-                                           float(dir_tol), int(probe_stride), float(probe_tol),
+        gate = GateCfg(float(tau), float(band), float(axis), float(dir_tol), int(probe_stride),
+                       float(probe_tol))
+        _check(self.lib.gt_surrogate_infer(tracer.ctx, self.h, ctypes.byref(gate),
                                            int(n_steps), float(step_precision), int(mode),
                                            *[_ptr(out[k]) for k in ("t", "r", "th", "ph",
                                                                     "status", "nsteps")],

@@ -651,6 +651,10 @@ def main():
     ap.add_argument("--batch-scale", type=int, default=8,
                     help="batch leg: camera sides divided by this factor")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="default launch shape instead of the autotuner's")
+    ap.add_argument("--rays-per-thread", type=int, default=0,
+                    help="with --no-autotune: FP32 rays per thread (1 or 2)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -690,6 +694,22 @@ def main():
     n = cam.n_rays
     out = tr.alloc_outputs(n)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    # launch shape from the autotuner (block size x resident blocks x rays per thread),
+    # timed on a central pixel range of this camera before the warm-up
+    launch = {"block_size": 128, "blocks_per_sm": 4, "rays_per_thread": 1, "autotuned": False}
+    if not args.no_autotune:
+        tr.set_camera(cam.r0, th0, cam.fov_deg, cam.res_x, cam.res_y)
+        b, k, rpt, v = tr.autotune(mode, trial_rays=1 << 16, trial_steps=300,
+                                   step_precision=wl.step_precision)
+        launch = {"block_size": b, "blocks_per_sm": k, "rays_per_thread": rpt, "autotuned": True,
+                  "trial_steps_per_s": v}
+    if args.no_autotune and args.rays_per_thread:
+        launch["rays_per_thread"] = args.rays_per_thread
+        if args.rays_per_thread == 2:
+            launch["blocks_per_sm"] = 3
+    opts = {k: launch[k] for k in ("block_size", "blocks_per_sm", "rays_per_thread")}
+    tr.set_options(**opts)
 
     for _ in range(args.warmup):
         tr.trace(wl.n_steps, wl.step_precision, mode, out)
@@ -764,6 +784,7 @@ def main():
         first = (cam.res_y // 2 - rows // 2) * cam.res_x
         cnt = rows * cam.res_x
         o64 = tr.alloc_outputs(cnt)
+        tr.set_options()  # the FP64 kernel at its default shape
         tr.trace_range(first + (rows // 2) * cam.res_x, cam.res_x, wl.n_steps, wl.step_precision,
                        geotrace.MODE_FP64, o64)  # warm-up: one row
         torch.cuda.synchronize()
@@ -799,7 +820,7 @@ def main():
         modes["surrogate"]["wall_s"] = time.perf_counter() - t0
     tr.set_spacetime(cam.M, cam.S, cam.Q)
     tr.set_camera(cam.r0, th0, cam.fov_deg, cam.res_x, cam.res_y)
-    tr.set_options()
+    tr.set_options(**opts)
 
     # ---------------- end to end through the host-pointer C-ABI call
     e2e = None
@@ -859,6 +880,7 @@ def main():
                        "step_precision": wl.step_precision,
                        "mode": "fp32_mixed" if mode else "fp64_plain",
                        "parallelism": f"rays sharded by camera, {world} rank(s)",
+                       "launch": launch,
                        "l2": "flushed between timed steps (256 MiB write, outside the events); "
                              "the kernel reads no input arrays"},
             "rays_per_s": rays_per_s,

@@ -87,3 +87,24 @@ def neighbour_band(status, res_x, res_y):
             sh[yd, xd] = s[ys, xs]
             m |= (sh != 255) & (sh != s)
     return m.ravel()
+
+
+def sensitive_rays(oracle, cam, n_steps, sp, ref, eps=1e-13, thresh=1e-10, threads=16):
+    """Rays of a camera whose oracle end state moves by more than `thresh` (relative, per
+    component) when the initial p_r is scaled by (1 + eps): chaotic rays, where the rounding
+    differences of two correct FP64 integrations (different but exact derivative routes)
+    grow past the parity tolerance.  `ref` is the unperturbed oracle result of the image."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    def one(k):
+        j, i = divmod(k, cam.res_x)
+        q, p = oracle.camera_ray(cam.M, cam.S, cam.Q, cam.r0, cam.theta0, cam.fov_deg,
+                                 cam.res_x, cam.res_y, i, j)
+        p = p.copy()
+        p[1] *= 1.0 + eps
+        qe, _, st, _, _ = oracle.trace_ray(cam.M, cam.S, cam.Q, q, p, cam.r0, n_steps, sp)
+        base = np.array([ref[x][k] for x in KEYS])
+        return st != ref["status"][k] or bool(np.any(
+            np.abs(qe - base) > thresh * np.maximum(1.0, np.abs(base))))
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        return np.array(list(ex.map(one, range(cam.res_x * cam.res_y))))

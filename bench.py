@@ -515,16 +515,16 @@ def oracle_sample(cam, n_steps, sp, pixels) -> dict:
 
 
 def mode_terminating(tr, geotrace, torch) -> dict:
-    """The paper's terminating workloads at the listing's 500,000-step cap, FP32-mixed:
-    the whole 1000x1000 Kerr a = 0.9M image, and a seeded pixel sample of the listing's
-    Manko-Novikov spacetime (its FP64 zone bounds it); each with its error against the
-    FP64 oracle on a pixel sample and the share of steps taken in the FP64 zone."""
+    """The paper's terminating workloads at the listing's 500,000-step cap, FP32-mixed, as
+    whole 1000x1000 images: Kerr a = 0.9M and the listing's Manko-Novikov spacetime (whose
+    trapped rays run in the FP64 zone); each with its error against the FP64 oracle on a
+    pixel sample (that sample's CPU baseline) and the share of steps taken in the zone."""
     import numpy as np
     res = {}
     cap, sp = 500000, 1.5e-4
     kerr = W.Camera(M=0.5, S=0.9 * 0.25, Q=0.0, r0=15.0, theta0=80 * W.DEG, fov_deg=75.0,
                     res_x=1000, res_y=1000)
-    cases = (("kerr1000_T", kerr, None, 32), ("mn1000_T", W.MN_1000, 4096, 16))
+    cases = (("kerr1000_T", kerr, None, 32), ("mn1000_T", W.MN_1000, None, 16))
     for name, cam, n_sample, n_judge in cases:
         tr.set_spacetime(cam.M, cam.S, cam.Q)
         tr.set_camera(cam.r0, cam.theta0, cam.fov_deg, cam.res_x, cam.res_y)
@@ -700,7 +700,7 @@ def main():
     launch = {"block_size": 128, "blocks_per_sm": 4, "rays_per_thread": 1, "autotuned": False}
     if not args.no_autotune:
         tr.set_camera(cam.r0, th0, cam.fov_deg, cam.res_x, cam.res_y)
-        b, k, rpt, v = tr.autotune(mode, trial_rays=1 << 16, trial_steps=300,
+        b, k, rpt, v = tr.autotune(mode, trial_rays=1 << 18, trial_steps=300,
                                    step_precision=wl.step_precision)
         launch = {"block_size": b, "blocks_per_sm": k, "rays_per_thread": rpt, "autotuned": True,
                   "trial_steps_per_s": v}

@@ -983,12 +983,26 @@ __global__ void __launch_bounds__(256, 1) trace2_kernel(TraceArgs A)
             if (drained) break;
             continue;
         }
-        // both steps back to back (an idle slot steps its last state; the result is unused)
-        const RayMixed keep0 = sl[0].m, keep1 = sl[1].m;
-        const float h0 = rk4_step32<KIND, PRECISE>(stf, sl[0].m, spf, w6f);
-        const float h1 = rk4_step32<KIND, PRECISE>(stf, sl[1].m, spf, w6f);
-        if (sl[0].active) finish(sl[0], h0, keep0);
-        if (sl[1].active) finish(sl[1], h1, keep1);
+        // both steps back to back (a lane's idle slot steps its last state and drops the
+        // result); a slot idle in the whole warp -- the queue's tail, or more slots than
+        // rays -- is skipped, a warp-uniform branch
+        const bool any0 = __any_sync(FULL_MASK, sl[0].active);
+        const bool any1 = __any_sync(FULL_MASK, sl[1].active);
+        if (any0 && any1) {
+            const RayMixed keep0 = sl[0].m, keep1 = sl[1].m;
+            const float h0 = rk4_step32<KIND, PRECISE>(stf, sl[0].m, spf, w6f);
+            const float h1 = rk4_step32<KIND, PRECISE>(stf, sl[1].m, spf, w6f);
+            if (sl[0].active) finish(sl[0], h0, keep0);
+            if (sl[1].active) finish(sl[1], h1, keep1);
+        } else if (any0) { // static slot indices keep the slots in registers
+            const RayMixed keep = sl[0].m;
+            const float h = rk4_step32<KIND, PRECISE>(stf, sl[0].m, spf, w6f);
+            if (sl[0].active) finish(sl[0], h, keep);
+        } else {
+            const RayMixed keep = sl[1].m;
+            const float h = rk4_step32<KIND, PRECISE>(stf, sl[1].m, spf, w6f);
+            if (sl[1].active) finish(sl[1], h, keep);
+        }
     }
 }
 

@@ -64,6 +64,8 @@ WORKLOADS = {
 # smaller cases of the same kernels, for profiler captures
 WORKLOADS["mn256"] = Workload("mn256", dataclasses.replace(MN_1000, res_x=256, res_y=256),
                               20000, 1.5e-4)
+WORKLOADS["mn512"] = Workload("mn512", dataclasses.replace(MN_1000, res_x=512, res_y=512),
+                              20000, 1.5e-4)
 WORKLOADS["mn256_short"] = Workload("mn256_short",
                                     dataclasses.replace(MN_1000, res_x=256, res_y=256),
                                     2000, 1.5e-4)

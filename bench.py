@@ -100,7 +100,7 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ ncu traffic record
 # sources that define the ray-tracing kernels (a traffic record stays valid while they do)
-TRACE_SOURCES = ("trace.cu", "spacetime.cuh", "internal.cuh", "camera.cuh")
+TRACE_SOURCES = ("trace.cu", "spacetime.cuh", "internal.cuh", "camera.cuh", "compensated.cuh")
 
 
 def source_sha1() -> str:
@@ -242,8 +242,9 @@ def leg_batch(tr, geotrace, args, torch):
 def leg_surrogate(tr, geotrace, args, torch):
     """Surrogate: label sg_samples rays with the integrator (FP32-mixed, 500,000-step cap)
     over the batch ranges at r0 = 30M, train, then image a sg_res^2 Kerr camera (a = 0.9M,
-    80 deg) with gating + integrator fallback; integrator-only time from a pixel subsample;
-    accuracy against the FP64 integrator on a 64x64 pixel subsample."""
+    80 deg) with the gates alone and with integrator probes + fallback; integrator-only
+    time from a pixel subsample; accuracy against the FP64 integrator on a 64x64 pixel
+    subsample (the network's pixels among them)."""
     import numpy as np
     M, r0, sp, cap = 0.5, 15.0, 1.5e-4, 500000
     host = W.surrogate_samples(args.sg_samples, seed=15183, M=M, r0=r0)
@@ -290,32 +291,95 @@ def leg_surrogate(tr, geotrace, args, torch):
              np.sin(a_th) * np.sin(b_th) * np.sin((b_ph - a_ph) / 2) ** 2)
         return 2 * np.arcsin(np.sqrt(np.clip(h, 0, 1)))
 
-    def accuracy(got):
-        same = (got["status"] == 0) == (jd["status"] == 0)
-        both = (got["status"] == 0) & (jd["status"] == 0)
-        ang = angle(got["th"][both], got["ph"][both], jd["th"][both], jd["ph"][both])
-        return {"classification_agreement": float(same.mean()),
+    def accuracy(got, ref=None):
+        ref = jd if ref is None else ref
+        same = (got["status"] == 0) == (ref["status"] == 0)
+        both = (got["status"] == 0) & (ref["status"] == 0)
+        ang = angle(got["th"][both], got["ph"][both], ref["th"][both], ref["ph"][both])
+        return {"classification_agreement": float(same.mean()) if same.size else 1.0,
                 "angle_err_max": float(ang.max()) if ang.size else 0.0,
                 "angle_err_p99": float(np.percentile(ang, 99)) if ang.size else 0.0,
                 "angle_err_median": float(np.median(ang)) if ang.size else 0.0}
 
     res["fp32_mixed_vs_fp64"] = accuracy(md)
-    for tau, band, dtol in ((2.0, 0.02, 0.0), (4.0, 0.05, 0.0), (2.0, 0.02, 0.005)):
+    settings = (("tau2_band0.02", dict(tau=2.0, band=0.02)),
+                ("tau2_band0.02_dirtol0.005", dict(tau=2.0, band=0.02, dir_tol=0.005)),
+                ("probes8_tol1e-3_axis0.02", dict(tau=2.0, band=0.02, axis=0.02, probe_stride=8,
+                                                  probe_tol=1e-3)),
+                ("probes32_tol1e-3_axis0.02", dict(tau=2.0, band=0.02, axis=0.02,
+                                                   probe_stride=32, probe_tol=1e-3)))
+    for name, gate in settings:
         out = tr.alloc_outputs(cam.n_rays)
-        (out, nfb), t_inf = _timed(torch, tr.stream,
-                                   lambda: sg.infer(tr, tau, band, cap, sp,
-                                                    geotrace.MODE_FP32_MIXED, out=out,
-                                                    dir_tol=dtol))
+        gate = dict(gate)
+        tau, band = gate.pop("tau"), gate.pop("band")
+        run = lambda: sg.infer(tr, tau, band, cap, sp, geotrace.MODE_FP32_MIXED, out=out,
+                               with_probes=True, **gate)
+        (out, nfb, npr), t_inf = _timed(torch, tr.stream, run)
         got = {k: out[k][torch.tensor(judge_pix, device="cuda")].cpu().numpy()
-               for k in ("status", "th", "ph")}
-        res[f"tau{tau}_band{band}" + (f"_dirtol{dtol}" if dtol else "")] = {
-            "seconds": t_inf, "fallback_pixels": nfb, "fallback_frac": nfb / cam.n_rays,
-            "speedup_vs_integrator_only": integ_full_s / t_inf, **accuracy(got)}
+               for k in ("status", "th", "ph", "nsteps")}
+        net = got["nsteps"].view(np.uint32) == 0  # judge the network's pixels
+        res[name] = {
+            "seconds": t_inf, "fallback_pixels": nfb, "probe_pixels": npr,
+            "integrated_frac": (nfb + npr) / cam.n_rays,
+            "speedup_vs_integrator_only": integ_full_s / t_inf,
+            "judged_network_pixels": int(net.sum()),
+            **accuracy({k: v[net] for k, v in got.items()},
+                       {k: v[net] for k, v in jd.items()})}
     res["integrator_only_seconds_extrapolated"] = integ_full_s
     res["integrator_subsample"] = f"{sub_pix.numel()} pixels (every {sub_step}th in x and y)"
     res["judge"] = f"FP64 integrator on {judge_pix.size} pixels (every {step}th in x and y)"
     sg.close()
     return res
+
+
+def leg_surrogate_mn(tr, geotrace, args, torch):
+    """A surrogate with the Manko-Novikov deviation as a live input: label 2^21 rays with
+    q ~ U[-2, 2], a/M ~ U[0.1, 0.99], inclination ~ U[5, 90] deg at r0 = 30M (FP32-mixed,
+    500,000-step cap), train, and image the listing's spacetime (q = 2, S = 0.24) at 80 deg,
+    1024^2, with integrator probes every 8 pixels (tolerance 1e-3), the axis gate and
+    fallback; against integrator-only on the same image (time) and the FP64 integrator on
+    4096 of the network's pixels (error)."""
+    import numpy as np
+    M, r0, sp, cap = 0.5, 15.0, 1.5e-4, 500000
+    host = W.surrogate_samples(1 << 21, seed=2310, M=M, r0=r0, q_max=2.0)
+    dev = [torch.tensor(x, dtype=torch.float64, device="cuda") for x in host]
+    lab, t_label = _timed(torch, tr.stream,
+                          lambda: tr.trace_rays(*dev, M, r0, cap, sp, geotrace.MODE_FP32_MIXED))
+    sg = geotrace.Surrogate(0, r0=r0, seed=9)
+    t0 = time.perf_counter()
+    losses = sg.train(tr, dev, [lab["status"], lab["th"], lab["ph"]], epochs=80, batch=8192,
+                      lr=2e-3, dir_weight=100.0)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    cam = W.Camera(M=M, S=0.24, Q=2.0, r0=r0, theta0=80 * W.DEG, fov_deg=75.0, res_x=1024,
+                   res_y=1024)
+    tr.set_spacetime(cam.M, cam.S, cam.Q)
+    tr.set_camera(cam.r0, cam.theta0, cam.fov_deg, cam.res_x, cam.res_y)
+    tr.set_options()
+    full, t_full = _timed(torch, tr.stream, lambda: tr.trace(cap, sp, geotrace.MODE_FP32_MIXED))
+    out = tr.alloc_outputs(cam.n_rays)
+    run = lambda: sg.infer(tr, 2.0, 0.0, cap, sp, geotrace.MODE_FP32_MIXED, out=out,
+                           probe_stride=8, probe_tol=1e-3, axis=0.02, with_probes=True)
+    (out, nfb, npr), t_inf = _timed(torch, tr.stream, run)
+    ns = out["nsteps"].cpu().numpy().view(np.uint32)
+    net = np.flatnonzero(ns == 0)
+    judge = net[W.sample_pixels(net.size, min(4096, net.size), seed=43)]
+    ref = tr.trace_pixels(torch.tensor(judge, device="cuda"), cap, sp, geotrace.MODE_FP64)
+    torch.cuda.synchronize()
+    ref = {k: (v.cpu().numpy().view(np.uint32) if k == "nsteps" else v.cpu().numpy())
+           for k, v in ref.items()}
+    acc = accuracy(host_sample(out, judge), ref)
+    acc.pop("max_rel_err")
+    sg.close()
+    return {"train_rays": 1 << 21, "label_seconds": t_label, "train_seconds": t_train,
+            "loss_first_last": [float(losses[0]), float(losses[-1])],
+            "label_status_counts": {str(a): int(b) for a, b in zip(
+                *np.unique(lab["status"].cpu().numpy(), return_counts=True))},
+            "image": "listing's Manko-Novikov (q = 2, S = 0.24), 80 deg, 1024x1024",
+            "seconds": t_inf, "integrator_only_seconds": t_full,
+            "speedup_vs_integrator_only": t_full / t_inf, "probe_pixels": npr,
+            "fallback_pixels": nfb, "network_pixel_fraction": net.size / cam.n_rays,
+            "accuracy_vs_fp64": acc}
 
 
 def leg_gemm(geotrace, args, torch):
@@ -333,6 +397,8 @@ def leg_gemm(geotrace, args, torch):
     res["peak_hbm_gbs"] = hbm
     for name, (M, N, K, splits, bn) in {"forward_hidden": (1 << 20, 256, 256, 1, 128),
                                         "forward_hidden_bn256": (1 << 20, 256, 256, 1, 256),
+                                        # the split-precision forward: K' = 3 x 256
+                                        "forward_hidden_split_k768": (1 << 20, 256, 768, 1, 256),
                                         "weight_grad": (256, 256, 1 << 16, 128, 128)}.items():
         A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
         B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
@@ -642,7 +708,8 @@ def main():
     ap.add_argument("--sg-default-res", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--legs", default="",
-                    help="extra legs: batch,surrogate,sweep,gemm,paper,mn_sweep (comma list)")
+                    help="extra legs: batch,surrogate,surrogate_mn,sweep,gemm,paper,mn_sweep "
+                         "(comma list)")
     ap.add_argument("--sg-samples", type=int, default=1 << 22)
     ap.add_argument("--sg-epochs", type=int, default=120)
     ap.add_argument("--sg-batch", type=int, default=8192)
@@ -863,6 +930,8 @@ def main():
             legs["paper"] = leg_paper(tr, geotrace, args, torch)
         elif leg == "mn_sweep":
             legs["mn_sweep"] = leg_mn_sweep(tr, geotrace, args, torch)
+        elif leg == "surrogate_mn":
+            legs["surrogate_mn"] = leg_surrogate_mn(tr, geotrace, args, torch)
         else:
             raise SystemExit(f"unknown leg {leg}")
         legs[leg]["leg_wall_s"] = time.perf_counter() - t0

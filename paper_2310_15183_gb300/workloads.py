@@ -101,17 +101,19 @@ def batch_cameras(n_cams: int = 64, seed: int = 2310, M: float = 0.5,
 
 
 def surrogate_samples(n: int, seed: int = 15183, M: float = 0.5, fov_deg: float = 75.0,
-                      r0: float = 15.0):
+                      r0: float = 15.0, q_max: float = 0.0):
     """Training inputs of the surrogate: pixel direction (alpha, beta) uniform over the
     FOV square of a camera at r0, dimensionless spin a/M ~ U[0, 0.99] (S = (a/M) M^2),
-    q = 0, inclination ~ U[5, 90] deg.  Returns float64 arrays (alpha, beta, a/M, q,
-    theta0)."""
+    q = 0, inclination ~ U[5, 90] deg.  With q_max > 0 the Manko-Novikov deviation is a
+    live input, q ~ U[-q_max, q_max], and the spin is drawn from U[0.1, 0.99] (q != 0
+    needs S != 0; the paper's "non-rotating" Manko-Novikov holes use S = 0.1 M^2).
+    Returns float64 arrays (alpha, beta, a/M, q, theta0)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     V = math.tan(0.5 * fov_deg * DEG) / r0
     H = math.atan(math.tan(V))
     alpha = rng.uniform(-H, H, n)
     beta = rng.uniform(-V, V, n)
-    a = rng.uniform(0.0, 0.99, n)
-    q = np.zeros(n)
+    a = rng.uniform(0.1 if q_max > 0 else 0.0, 0.99, n)
+    q = rng.uniform(-q_max, q_max, n) if q_max > 0 else np.zeros(n)
     th0 = rng.uniform(5.0, 90.0, n) * DEG
     return alpha, beta, a, q, th0

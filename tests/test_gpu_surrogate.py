@@ -308,3 +308,38 @@ def test_probed_surrogate_meets_target_and_beats_the_integrator(g, tracer):
         assert t_sg < t_int, (t_sg, t_int)
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("rx,ry,stride", [(37, 29, 8), (16, 17, 5), (1, 9, 4), (2, 2, 8)])
+def test_probe_grid_on_ragged_and_degenerate_images(g, tracer, rx, ry, stride):
+    """Probe placement and bookkeeping on images whose sides are not multiples of the
+    stride (the last column and row are probes too) and on images too thin for a probe
+    cell (no probes): every integrated pixel -- probe or fallback -- carries exactly the
+    FP32-mixed integrator's result, the probe count is the grid's, and the probes are
+    integrated pixels."""
+    cam = W.Camera(M=0.5, S=0.45 * 0.5, Q=0.0, r0=15.0, theta0=70 * W.DEG, fov_deg=60.0,
+                   res_x=rx, res_y=ry)
+    tracer.set_spacetime(cam.M, cam.S, cam.Q)
+    tracer.set_camera(cam.r0, cam.theta0, cam.fov_deg, rx, ry)
+    tracer.set_options()
+    s = g.Surrogate(0, seed=21)
+    try:
+        out, nfb, npr = s.infer(tracer, 1.0, 0.0, 300000, 1.5e-4, g.MODE_FP32_MIXED,
+                                probe_stride=stride, probe_tol=1e-3, with_probes=True)
+        got = to_numpy(out)
+        mix = to_numpy(tracer.trace(300000, 1.5e-4, g.MODE_FP32_MIXED))
+        if rx >= 2 and ry >= 2:
+            cols = sorted(set(list(range(0, rx, stride)) + [rx - 1]))
+            rows = sorted(set(list(range(0, ry, stride)) + [ry - 1]))
+            assert npr == len(cols) * len(rows)
+            for j in rows:
+                for i in cols:
+                    assert got["nsteps"][j * rx + i] > 0
+        else:
+            assert npr == 0
+        integ = got["nsteps"] > 0
+        assert integ.sum() == nfb + npr
+        for k in ("status", "th", "ph", "t", "r", "nsteps"):
+            assert np.array_equal(got[k][integ], mix[k][integ]), k
+    finally:
+        s.close()

@@ -298,13 +298,15 @@ typedef struct gt_gate_cfg {
  * 2 x 2 pixels); their exact results go to the image, and each probe records the
  * network's error vector (exact unit end direction minus the predicted one).  A pixel
  * inside a probe cell is then taken from the network only when the cell's four corners
- * are classified alike by the integrator and the network -- all escaped, or all HORIZON
- * -- and, when escaping, the corners' error vectors differ by less than probe_tol
+ * are classified alike by the integrator and the network -- all escaped, or all not
+ * escaping with one common integrator status (HORIZON, or MAXSTEPS for rays still bound
+ * at the step cap), which the pixel takes -- and, when escaping, the corners' error
+ * vectors differ by less than probe_tol
  * (|e00 - e11| and |e01 - e10|); its end direction is the network's plus the bilinear
  * interpolation of the corner errors.  In every case a network pixel also passes the
  * gates of gt_gate_cfg.  Network pixels get status ESCAPED with end theta, phi from the
- * (corrected) direction, or HORIZON with NaN angles; t and r are NaN and nsteps 0 for
- * them.  All other pixels are traced by the integrator (mode, n_steps, step_precision as
+ * (corrected) direction, or HORIZON (MAXSTEPS inside an all-MAXSTEPS probe cell) with NaN
+ * angles; t and r are NaN and nsteps 0 for them.  All other pixels are traced by the integrator (mode, n_steps, step_precision as
  * gt_trace) and written in place.  Outputs as gt_trace (device, res_x*res_y each, none may
  * be NULL); *n_fallback receives the number of integrated pixels besides the probes,
  * *n_probes the number of probes (either may be NULL).  Errors: GT_ERR_INVALID_ARG (gate

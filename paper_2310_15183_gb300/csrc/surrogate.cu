@@ -371,9 +371,9 @@ __global__ void scatter_probes_kernel(int n, const int64_t *pix, const double *p
 
 // Decide per pixel: confident surrogate answer, or fall back to the integrator.  With
 // probes, a pixel is taken from the network only inside a probe cell whose four corners
-// the integrator and the network classify alike -- all escaped, or all captured
-// (HORIZON) -- and, for escaped ones, whose corner error vectors differ by less than
-// pg.tol; its end direction is the network's plus the bilinear interpolation of the
+// the integrator and the network classify alike -- all escaped, or all not escaping with
+// one common end (all HORIZON, or all MAXSTEPS: trapped; the pixel takes that status) --
+// and, for escaped ones, whose corner error vectors differ by less than pg.tol; its end direction is the network's plus the bilinear interpolation of the
 // corners' error vectors (the integrator correcting the network where it measured it).
 __global__ void gate_kernel(int64_t n, int64_t pix0, const CamDesc *cam, const float *Z5, float tau,
                             double band, double axis, float dir_tol, ProbeGrid pg, double *t, double *r,
@@ -390,6 +390,7 @@ __global__ void gate_kernel(int64_t n, int64_t pix0, const CamDesc *cam, const f
         const float logit = z[0];
         float nx = z[1], ny = z[2], nz = z[3];
         bool skip = false; // a probe: written by the integrator pass
+        int cap_status = GT_RAY_HORIZON; // status given to a captured network pixel
         if (pg.stride > 0) {
             if (is_probe(i, j, pg, res_x, res_y)) {
                 skip = true;
@@ -405,9 +406,13 @@ __global__ void gate_kernel(int64_t n, int64_t pix0, const CamDesc *cam, const f
                 const bool esc4 = c00.exact == GT_RAY_ESCAPED && c01.exact == GT_RAY_ESCAPED &&
                                   c10.exact == GT_RAY_ESCAPED && c11.exact == GT_RAY_ESCAPED &&
                                   c00.net_esc && c01.net_esc && c10.net_esc && c11.net_esc;
-                const bool cap4 = c00.exact == GT_RAY_HORIZON && c01.exact == GT_RAY_HORIZON &&
-                                  c10.exact == GT_RAY_HORIZON && c11.exact == GT_RAY_HORIZON &&
-                                  !c00.net_esc && !c01.net_esc && !c10.net_esc && !c11.net_esc;
+                // not escaping: the four corners end alike (all HORIZON, or all still
+                // bound at the step cap -- MAXSTEPS, the trapped rays of Manko-Novikov)
+                const bool cap4 = (c00.exact == GT_RAY_HORIZON || c00.exact == GT_RAY_MAXSTEPS) &&
+                                  c01.exact == c00.exact && c10.exact == c00.exact &&
+                                  c11.exact == c00.exact && !c00.net_esc && !c01.net_esc &&
+                                  !c10.net_esc && !c11.net_esc;
+                cap_status = c00.exact;
                 if (logit > 0.0f) {
                     float sp = 0.0f, sq = 0.0f;
 #pragma unroll
@@ -454,7 +459,7 @@ __global__ void gate_kernel(int64_t n, int64_t pix0, const CamDesc *cam, const f
             } else {
                 th[pix] = nan("");
                 ph[pix] = nan("");
-                status[pix] = GT_RAY_HORIZON;
+                status[pix] = (uint8_t)cap_status;
             }
             t[pix] = nan("");
             r[pix] = nan("");

@@ -100,7 +100,8 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ ncu traffic record
 # sources that define the ray-tracing kernels (a traffic record stays valid while they do)
-TRACE_SOURCES = ("trace.cu", "spacetime.cuh", "internal.cuh", "camera.cuh", "compensated.cuh")
+TRACE_SOURCES = ("trace.cu", "spacetime.cuh", "internal.cuh", "camera.cuh", "compensated.cuh",
+                 "df.cuh", "zone_df.cuh")
 
 
 def source_sha1() -> str:
@@ -373,7 +374,16 @@ def leg_surrogate_mn(tr, geotrace, args, torch):
     acc = accuracy(host_sample(out, judge), ref)
     acc.pop("max_rel_err")
     sg.close()
-    return {"train_rays": 1 << 21, "label_seconds": t_label, "train_seconds": t_train,
+    # where the integrator's share of the image goes: the integrator-only image's status of
+    # the pixels that gated inference integrated, and of all pixels
+    fst = full["status"].cpu().numpy()
+    ost = out["status"].cpu().numpy()
+    counts = lambda a: {str(x): int(y) for x, y in zip(*np.unique(a, return_counts=True))}
+    return {"integrated_pixels_status_in_full_image": counts(fst[ns > 0]),
+            "full_image_status_counts": counts(fst),
+            "network_pixels_status_agreement_with_full_image": float(
+                np.mean(ost[net] == fst[net])) if net.size else None,
+            "train_rays": 1 << 21, "label_seconds": t_label, "train_seconds": t_train,
             "loss_first_last": [float(losses[0]), float(losses[-1])],
             "label_status_counts": {str(a): int(b) for a, b in zip(
                 *np.unique(lab["status"].cpu().numpy(), return_counts=True))},
@@ -514,7 +524,8 @@ def leg_paper(tr, geotrace, args, torch):
 def leg_mn_sweep(tr, geotrace, args, torch):
     """Inclination sweep of the listing's Manko-Novikov spacetime (q = 2, S = 0.24, r0 =
     30M, FOV 75 deg) at the 500,000-step cap, frames theta0 = 5, 35, 62, 90 deg, whole
-    1000x1000 images, FP32-mixed; status counts and the FP64-zone share of the steps.
+    1000x1000 images, FP32-mixed; status counts, the zone's share of the steps and the
+    share of its field evaluations done in FP64.
     (Small pixel samples are timed by the few trapped rays that run the whole cap one after
     another, not by throughput, so whole images are traced.)"""
     import numpy as np
@@ -525,13 +536,54 @@ def leg_mn_sweep(tr, geotrace, args, torch):
         tr.set_options()
         out, t = _timed(torch, tr.stream,
                         lambda: tr.trace(500000, 1.5e-4, geotrace.MODE_FP32_MIXED))
-        zone = tr.zone_steps()
+        zone, zone_f64 = tr.zone_stats()
         steps = _steps(out)
         st = out["status"].cpu().numpy()
         res[f"theta0_{th_deg:g}"] = {
             "seconds": t, "steps_per_s": steps / t, "seconds_per_mpx": t,
             "status_counts": {str(a): int(b) for a, b in zip(*np.unique(st, return_counts=True))},
-            "fp64_zone_step_fraction": zone / steps}
+            "zone_step_fraction": zone / steps,
+            "zone_f64_eval_fraction": zone_f64 / (4 * zone) if zone else 0.0}
+    return res
+
+
+def leg_zone(tr, geotrace, args, torch):
+    """The listing's Manko-Novikov image (1000x1000, 500,000-step cap, FP32-mixed) with the
+    zone's field in double-float (the default) and in FP64 (GT_FLAG_ZONE_FP64): the time of
+    each whole image, the zone statistics, and the agreement of the two images (status of
+    every pixel; end angle of the pixels both call escaped), with both against the FP64
+    integrator on 256 seeded pixels that are not trapped (the trapped rays' end states at
+    the cap are chaotic)."""
+    import numpy as np
+    cam = W.MN_1000
+    tr.set_spacetime(cam.M, cam.S, cam.Q)
+    tr.set_camera(cam.r0, cam.theta0, cam.fov_deg, cam.res_x, cam.res_y)
+    res, outs = {}, {}
+    for name, flags in (("double_float", 0), ("fp64", geotrace.FLAG_ZONE_FP64)):
+        tr.set_options(flags=flags)
+        out, t = _timed(torch, tr.stream,
+                        lambda: tr.trace(500000, 1.5e-4, geotrace.MODE_FP32_MIXED))
+        zone, f64 = tr.zone_stats()
+        steps = _steps(out)
+        outs[name] = host_sample(out, slice(None))
+        st = outs[name]["status"]
+        res[name] = {"seconds": t, "steps_per_s": steps / t,
+                     "status_counts": {str(a): int(b) for a, b in
+                                       zip(*np.unique(st, return_counts=True))},
+                     "zone_step_fraction": zone / steps,
+                     "zone_f64_eval_fraction": f64 / (4 * zone) if zone else 0.0}
+    tr.set_options()
+    res["double_float_vs_fp64_zone"] = accuracy(outs["double_float"], outs["fp64"])
+    res["speedup"] = res["fp64"]["seconds"] / res["double_float"]["seconds"]
+    st = outs["fp64"]["status"]
+    cand = np.flatnonzero(st != 2)
+    pix = cand[W.sample_pixels(cand.size, 256, seed=77)]
+    ref = tr.trace_pixels(torch.tensor(pix, device="cuda"), 500000, 1.5e-4,
+                          geotrace.MODE_FP64)
+    ref = host_sample(ref, slice(None))
+    for name in ("double_float", "fp64"):
+        acc = accuracy({k: v[pix] for k, v in outs[name].items()}, ref)
+        res[name]["vs_fp64_integrator_256_untrapped_pixels"] = acc
     return res
 
 
@@ -583,7 +635,7 @@ def oracle_sample(cam, n_steps, sp, pixels) -> dict:
 def mode_terminating(tr, geotrace, torch) -> dict:
     """The paper's terminating workloads at the listing's 500,000-step cap, FP32-mixed, as
     whole 1000x1000 images: Kerr a = 0.9M and the listing's Manko-Novikov spacetime (whose
-    trapped rays run in the FP64 zone); each with its error against the FP64 oracle on a
+    trapped rays run in the zone); each with its error against the FP64 oracle on a
     pixel sample (that sample's CPU baseline) and the share of steps taken in the zone."""
     import numpy as np
     res = {}
@@ -605,7 +657,7 @@ def mode_terminating(tr, geotrace, torch) -> dict:
             run = lambda: tr.trace_pixels(dpix, cap, sp, geotrace.MODE_FP32_MIXED)
             n = n_sample
         out, t = _timed(torch, tr.stream, run)
-        zone = tr.zone_steps()
+        zone, zone_f64 = tr.zone_stats()
         steps = _steps(out)
         st = out["status"].cpu().numpy()
         judge = W.sample_pixels(n, n_judge, seed=32)
@@ -617,7 +669,8 @@ def mode_terminating(tr, geotrace, torch) -> dict:
             "rays": n, "seconds": t, "steps_per_s": steps / t, "rays_per_s": n / t,
             "seconds_per_mpx": t * 1e6 / n, "mean_steps_per_ray": steps / n,
             "status_counts": {str(a): int(b) for a, b in zip(*np.unique(st, return_counts=True))},
-            "fp64_zone_step_fraction": zone / steps if steps else 0.0,
+            "zone_step_fraction": zone / steps if steps else 0.0,
+            "zone_f64_eval_fraction": zone_f64 / (4 * zone) if zone else 0.0,
             "sample": "whole image" if pix is None else f"{n} seeded pixels of 1000x1000",
             "accuracy_vs_oracle": accuracy(got, ref),
             "cpu_baseline": {"value": float(ref["nsteps"].astype(np.float64).sum()) / t_cpu,
@@ -708,7 +761,7 @@ def main():
     ap.add_argument("--sg-default-res", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--legs", default="",
-                    help="extra legs: batch,surrogate,surrogate_mn,sweep,gemm,paper,mn_sweep "
+                    help="extra legs: batch,surrogate,surrogate_mn,sweep,gemm,paper,mn_sweep,zone "
                          "(comma list)")
     ap.add_argument("--sg-samples", type=int, default=1 << 22)
     ap.add_argument("--sg-epochs", type=int, default=120)
@@ -930,6 +983,8 @@ def main():
             legs["paper"] = leg_paper(tr, geotrace, args, torch)
         elif leg == "mn_sweep":
             legs["mn_sweep"] = leg_mn_sweep(tr, geotrace, args, torch)
+        elif leg == "zone":
+            legs["zone"] = leg_zone(tr, geotrace, args, torch)
         elif leg == "surrogate_mn":
             legs["surrogate_mn"] = leg_surrogate_mn(tr, geotrace, args, torch)
         else:

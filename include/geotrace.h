@@ -60,8 +60,10 @@ extern "C" {
 
 /* arithmetic modes */
 #define GT_MODE_FP64 0       /* FP64 end to end */
-#define GT_MODE_FP32_MIXED 1 /* FP32 RK4 with compensated state; FP64 zone and H = 0 re-projection.
-                              * Runs in rounds (FP32 launch, FP64-zone launch, ...) and returns
+#define GT_MODE_FP32_MIXED 1 /* FP32 RK4 with compensated state; a zone r < r_switch stepped with
+                              * an FP64 state (its Manko-Novikov field in double-float where the
+                              * evaluation's range allows, else FP64) and H = 0 re-projection.
+                              * Runs in rounds (FP32 launch, zone launch, ...) and returns
                               * once the work has completed. */
 
 /* option flags */
@@ -73,6 +75,9 @@ extern "C" {
                                   * launch; FP32-mixed runs its rounds under a conditional WHILE
                                   * node whose condition the device sets, so the call stays
                                   * asynchronous.  Not with GT_FLAG_ONE_SHOT. */
+#define GT_FLAG_ZONE_FP64 256    /* FP32-mixed, Manko-Novikov: evaluate the zone's field in FP64
+                                  * throughout instead of double-float (two floats, ~48 bits,
+                                  * on the FP32 pipes) */
 #define GT_FLAG_PRECISE_MN 16    /* FP32-mixed, Manko-Novikov: evaluate the metric's multipole
                                   * sums as closed-form series tails, free of the cancellation
                                   * that costs the plain FP32 form ~2 beta ulp(1) in its
@@ -95,7 +100,7 @@ typedef struct gt_options {
     int blocks_per_sm;       /* persistent grid = min(blocks_per_sm, resident limit) * SMs; 0 = 4 */
     int flags;               /* GT_FLAG_* */
     int reproject_every;     /* FP32-mixed: steps between H = 0 re-projections; 0 = 4096 */
-    double r_switch;         /* FP32-mixed: FP64 zone r < r_switch; < 0 = none; 0 = automatic:
+    double r_switch;         /* FP32-mixed: zone r < r_switch; < 0 = none; 0 = automatic:
                                 none for Kerr, 4M for Manko-Novikov */
     double timeout_seconds;  /* device watchdog (wall clock per launch); 0 = none */
     int rays_per_thread;     /* FP32-mixed: rays each thread integrates at once, 1 or 2 (two
@@ -293,24 +298,27 @@ typedef struct gt_gate_cfg {
 } gt_gate_cfg;
 
 /* Image of the configured camera through the surrogate, with the integrator as judge and
- * fallback.  With gate->probe_stride > 0 the integrator first traces the probe pixels
+ * fallback.  The network runs on every pixel first.  With gate->probe_stride > 0 the pixels
  * (i, j) with i, j multiples of probe_stride or the last column/row (images of at least
- * 2 x 2 pixels); their exact results go to the image, and each probe records the
- * network's error vector (exact unit end direction minus the predicted one).  A pixel
- * inside a probe cell is then taken from the network only when the cell's four corners
- * are classified alike by the integrator and the network -- all escaped, or all not
- * escaping with one common integrator status (HORIZON, or MAXSTEPS for rays still bound
- * at the step cap), which the pixel takes -- and, when escaping, the corners' error
- * vectors differ by less than probe_tol
+ * 2 x 2 pixels) are probes: the integrator traces them, their exact results go to the image,
+ * and each probe records the network's error vector (exact unit end direction minus the
+ * predicted one).  A pixel inside a probe cell is then taken from the network only when the
+ * cell's four corners are classified alike by the integrator and the network -- all escaped,
+ * or all not escaping with one common integrator status (HORIZON, or MAXSTEPS for rays still
+ * bound at the step cap), which the pixel takes -- the pixel's own prediction agrees with
+ * theirs, and, when escaping, the corners' error vectors differ by less than probe_tol
  * (|e00 - e11| and |e01 - e10|); its end direction is the network's plus the bilinear
- * interpolation of the corner errors.  In every case a network pixel also passes the
- * gates of gt_gate_cfg.  Network pixels get status ESCAPED with end theta, phi from the
+ * interpolation of the corner errors.  In every case a network pixel also passes the gates
+ * of gt_gate_cfg.  Network pixels get status ESCAPED with end theta, phi from the
  * (corrected) direction, or HORIZON (MAXSTEPS inside an all-MAXSTEPS probe cell) with NaN
- * angles; t and r are NaN and nsteps 0 for them.  All other pixels are traced by the integrator (mode, n_steps, step_precision as
- * gt_trace) and written in place.  Outputs as gt_trace (device, res_x*res_y each, none may
- * be NULL); *n_fallback receives the number of integrated pixels besides the probes,
- * *n_probes the number of probes (either may be NULL).  Errors: GT_ERR_INVALID_ARG (gate
- * NULL or out of range, NULL outputs) and those of gt_trace.  Synchronous. */
+ * angles; t and r are NaN and nsteps 0 for them.  All other pixels are traced by the
+ * integrator (mode, n_steps, step_precision as gt_trace) and written in place: in one
+ * launch with the probes, the pixels that the network's answers alone send there (a gate,
+ * or a prediction differing from a corner's), in a second one those that the probes'
+ * results send there.  Outputs as gt_trace (device, res_x*res_y each, none may be NULL);
+ * *n_fallback receives the number of integrated pixels besides the probes, *n_probes the
+ * number of probes (either may be NULL).  Errors: GT_ERR_INVALID_ARG (gate NULL or out of
+ * range, NULL outputs) and those of gt_trace.  Synchronous. */
 int gt_surrogate_infer(gt_ctx *ctx, gt_surrogate *s, const gt_gate_cfg *gate, int64_t n_steps,
                        double step_precision, int mode, double *t, double *r, double *theta,
                        double *phi, uint8_t *status, uint32_t *nsteps, int64_t *n_fallback,
@@ -329,11 +337,11 @@ int gt_surrogate_get_grads(gt_surrogate *s, float *host, int64_t n);
  * is not acceptable.  The paper has no counterpart.
  *
  * No context is needed and nothing is allocated: the queue counter and the camera
- * descriptors live in one static device array of the library (about 18 KB for
+ * descriptors live in one static device array of the library (about 22 KB for
  * GT_NOALLOC_MAX_CAMS cameras), which every device that loads the library holds until
  * the process exits.  The caller still owns and passes the device output arrays
  * (layout as gt_trace_batch; default launch options, no watchdog).  In FP32-mixed
- * mode the FP64 zone steps run inline in the FP32 kernel (H = 0 re-projection every
+ * mode the zone steps run inline in the FP32 kernel (H = 0 re-projection every
  * 4096 steps, the context's default), because the park lists gt_trace_batch uses would
  * need allocated memory; FP64 results are identical to gt_trace_batch's.  Each call
  * looks up that array's device address on `device` once per process (with the device
@@ -364,10 +372,13 @@ int gt_autotune(gt_ctx *ctx, int mode, int64_t trial_rays, int64_t trial_steps,
 /* Wait for all work issued by the context. */
 int gt_sync(gt_ctx *ctx);
 
-/* RK4 steps the last trace of the context took in the FP64 zone of GT_MODE_FP32_MIXED
- * (0 for FP64 traces and for mixed traces that never entered it); compare with the sum
- * of nsteps for the zone's share of the work.  Synchronises the context's stream. */
-int gt_get_stats(gt_ctx *ctx, int64_t *zone_steps);
+/* RK4 steps the last trace of the context took in the zone of GT_MODE_FP32_MIXED (0 for
+ * FP64 traces and for mixed traces that never entered it; compare with the sum of nsteps
+ * for the zone's share of the work) and, in zone_f64_evals (may be NULL), the field
+ * evaluations of those steps done in FP64 (all of them with GT_FLAG_ZONE_FP64; otherwise
+ * the Manko-Novikov evaluations outside the double-float range).  Synchronises the
+ * context's stream. */
+int gt_get_stats(gt_ctx *ctx, int64_t *zone_steps, int64_t *zone_f64_evals);
 
 /* Number of streaming multiprocessors of the context's device (for grid sizing). */
 int gt_device_sm_count(gt_ctx *ctx, int *out);

@@ -54,26 +54,29 @@ struct gt_ctx {
     gt::RayParams *d_rays = nullptr;
     // spacetime descriptor of gt_trace_states (no camera)
     CamDesc *d_state_cam = nullptr;
-    // integrator probes of gated surrogate inference: pixel list, exact results, records
+    // gated surrogate inference: probe records; the network's answers (float4 per pixel)
+    // followed by an integrator pixel list
     void *d_probe = nullptr;
     int64_t probe_cap = 0;
-    int64_t *d_fallback = nullptr;
-    int64_t fallback_cap = 0;
+    void *d_infer = nullptr;
+    int64_t infer_cap = 0;
 };
 
 cudaStream_t gt_internal_stream(gt_ctx *c) { return c->stream; }
 
 namespace gt {
 namespace sg {
-int infer_chunks(gt_surrogate *s, const CamDesc *d_cam, int64_t n_pix, float tau, double band,
-                 double axis, float dir_tol, const ProbeGrid &pg, double *t, double *r, double *th, double *ph,
-                 uint8_t *status, uint32_t *nsteps, int64_t *d_fallback, unsigned long long *d_nfb,
-                 cudaStream_t st);
-int probe_pixels(const CamDesc *d_cam, const ProbeGrid &pg, int64_t *d_pix, cudaStream_t st);
-int probe_records(gt_surrogate *s, const CamDesc *d_cam, const int64_t *d_pix, int n,
-                  const double *pt, const double *pr, const double *pth, const double *pph,
-                  const uint8_t *pst, const uint32_t *pns, ProbeRec *rec, double *t, double *r,
-                  double *th, double *ph, uint8_t *status, uint32_t *nsteps, cudaStream_t st);
+int net_pass(gt_surrogate *s, const CamDesc *d_cam, int64_t n_pix, float4 *net, cudaStream_t st);
+int select_first(const CamDesc *d_cam, int64_t n_pix, const float4 *net, const ProbeGrid &pg,
+                 float tau, double band, double axis, float dir_tol, int64_t *list,
+                 unsigned long long *count, cudaStream_t st);
+int probe_records(const CamDesc *d_cam, const ProbeGrid &pg, const float4 *net,
+                  const uint8_t *status, const double *th, const double *ph, ProbeRec *rec,
+                  cudaStream_t st);
+int gate_rest(const CamDesc *d_cam, int64_t n_pix, const float4 *net, const ProbeGrid &pg,
+              float tau, double band, double axis, float dir_tol, double *t, double *r, double *th,
+              double *ph, uint8_t *status, uint32_t *nsteps, int64_t *list,
+              unsigned long long *count, cudaStream_t st);
 } // namespace sg
 } // namespace gt
 
@@ -395,6 +398,7 @@ int run_trace(gt_ctx *c, const CamDesc *d_cams, int n_cams, int kind_hint, int64
     a.scratch = c->d_scratch;
     a.euler = (e.flags & GT_FLAG_EULER) ? 1 : 0;
     a.f32_io = (e.flags & GT_FLAG_F32_IO) ? 1 : 0;
+    a.zone_df = (e.flags & GT_FLAG_ZONE_FP64) ? 0 : 1;
     a.disk = x.disk;
     a.z = x.z;
     a.states = x.states;
@@ -553,7 +557,7 @@ int gt_destroy(gt_ctx *c)
     cudaFree(c->d_stage);
     cudaFree(c->d_park);
     cudaFree(c->d_rays);
-    cudaFree(c->d_fallback);
+    cudaFree(c->d_infer);
     cudaFree(c->d_state_cam);
     cudaFree(c->d_probe);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
@@ -606,7 +610,7 @@ int gt_set_options(gt_ctx *c, const gt_options *o)
     if (!isfinite(v.r_switch) || !(v.timeout_seconds >= 0.0) || !isfinite(v.timeout_seconds))
         return GT_ERR_INVALID_ARG;
     if (v.flags & ~(GT_FLAG_COMPAT_WEIGHTS | GT_FLAG_COMPAT_CAMERA | GT_FLAG_ONE_SHOT |
-                    GT_FLAG_GRAPH | GT_FLAG_PRECISE_MN | PAPER_FLAGS))
+                    GT_FLAG_GRAPH | GT_FLAG_PRECISE_MN | GT_FLAG_ZONE_FP64 | PAPER_FLAGS))
         return GT_ERR_INVALID_ARG;
     c->opts = v;
     return GT_OK;
@@ -879,66 +883,81 @@ int gt_surrogate_infer(gt_ctx *c, gt_surrogate *s, const gt_gate_cfg *gate, int6
     if (rc != GT_OK) return rc;
     if (!c->cam_valid) return GT_ERR_INVALID_ARG;
     const int64_t n_pix = (int64_t)c->res_x * c->res_y;
-    if (c->fallback_cap < n_pix) {
+    if (c->infer_cap < n_pix) {
         cudaStreamSynchronize(c->stream);
-        cudaFree(c->d_fallback);
-        c->d_fallback = nullptr;
-        c->fallback_cap = 0;
-        cudaError_t e = cudaMalloc(&c->d_fallback, n_pix * sizeof(int64_t));
+        cudaFree(c->d_infer);
+        c->d_infer = nullptr;
+        c->infer_cap = 0;
+        cudaError_t e = cudaMalloc(&c->d_infer, n_pix * (sizeof(float4) + sizeof(int64_t)));
         if (e != cudaSuccess) return cuda_code(e);
-        c->fallback_cap = n_pix;
+        c->infer_cap = n_pix;
     }
+    float4 *net = (float4 *)c->d_infer;
+    int64_t *list = (int64_t *)(net + n_pix);
     const int kind = (c->Q != 0.0) ? gt::KIND_MN : gt::KIND_KERR;
     // integrator probes on a grid of the given stride (images of at least 2 x 2 pixels)
     gt::sg::ProbeGrid pg = {};
+    int64_t np = 0;
     if (probe_stride > 0 && c->res_x >= 2 && c->res_y >= 2) {
         pg.stride = probe_stride;
         pg.nx = (c->res_x - 2) / probe_stride + 2;
         pg.ny = (c->res_y - 2) / probe_stride + 2;
         pg.tol = probe_tol;
-        const int64_t np = (int64_t)pg.nx * pg.ny;
-        const size_t per = 8 + 4 * 8 + 4 + 1 + sizeof(gt::sg::ProbeRec);
+        np = (int64_t)pg.nx * pg.ny;
         if (c->probe_cap < np) {
             cudaStreamSynchronize(c->stream);
             cudaFree(c->d_probe);
             c->d_probe = nullptr;
             c->probe_cap = 0;
-            cudaError_t e = cudaMalloc(&c->d_probe, np * per + 256);
+            cudaError_t e = cudaMalloc(&c->d_probe, np * sizeof(gt::sg::ProbeRec));
             if (e != cudaSuccess) return cuda_code(e);
             c->probe_cap = np;
         }
-        int64_t *pix = (int64_t *)c->d_probe;
-        double *pt = (double *)(pix + np), *pr = pt + np, *pth = pr + np, *pph = pth + np;
-        gt::sg::ProbeRec *rec = (gt::sg::ProbeRec *)(pph + np);
-        uint32_t *pns = (uint32_t *)(rec + np);
-        uint8_t *pst = (uint8_t *)(pns + np);
-        rc = gt::sg::probe_pixels(c->d_cam, pg, pix, c->stream);
-        if (rc == GT_OK)
-            rc = run_trace(c, c->d_cam, 1, kind, 0, np, n_steps, sp, mode, pt, pr, pth, pph, pst,
-                           pns, pix, nullptr, true);
-        if (rc == GT_OK)
-            rc = gt::sg::probe_records(s, c->d_cam, pix, (int)np, pt, pr, pth, pph, pst, pns, rec,
-                                       t, r, th, ph, status, nsteps, c->stream);
+    }
+    // count of a list; the word is free until the integrator runs, and is read back first
+    unsigned long long *d_count = c->d_scratch + gt::SCR_TO32;
+    auto list_count = [&](int64_t *out) -> int {
+        unsigned long long h = 0;
+        cudaError_t e = cudaMemcpyAsync(&h, d_count, sizeof h, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_code(e);
+        *out = (int64_t)h;
+        return GT_OK;
+    };
+    // 1. the network on every pixel
+    rc = gt::sg::net_pass(s, c->d_cam, n_pix, net, c->stream);
+    if (rc != GT_OK) return rc;
+    // 2. the probes and every pixel the network's answers alone send to the integrator
+    cudaError_t err = cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), c->stream);
+    if (err != cudaSuccess) return cuda_code(err);
+    rc = gt::sg::select_first(c->d_cam, n_pix, net, pg, tau, band, axis, dir_tol, list, d_count,
+                              c->stream);
+    int64_t n1 = 0, n2 = 0;
+    if (rc == GT_OK) rc = list_count(&n1);
+    if (rc == GT_OK && n1 > 0)
+        rc = run_trace(c, c->d_cam, 1, kind, 0, n1, n_steps, sp, mode, t, r, th, ph, status,
+                       nsteps, list, nullptr);
+    if (rc != GT_OK) return rc;
+    // 3. probe records from the traced probes
+    if (pg.stride > 0) {
+        gt::sg::ProbeRec *rec = (gt::sg::ProbeRec *)c->d_probe;
+        rc = gt::sg::probe_records(c->d_cam, pg, net, status, th, ph, rec, c->stream);
         if (rc != GT_OK) return rc;
         pg.rec = rec;
-        if (n_probes) *n_probes = np;
-    } else if (n_probes) {
-        *n_probes = 0;
     }
-    unsigned long long *d_nfb = c->d_scratch + gt::SCR_TO32; // free until the fallback trace
-    cudaError_t err = cudaMemsetAsync(d_nfb, 0, sizeof(unsigned long long), c->stream);
+    // 4. the rest from the network where the probe cells hold, else to a second list
+    err = cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), c->stream);
     if (err != cudaSuccess) return cuda_code(err);
-    rc = gt::sg::infer_chunks(s, c->d_cam, n_pix, tau, band, axis, dir_tol, pg, t, r, th, ph,
-                              status, nsteps, c->d_fallback, d_nfb, c->stream);
+    rc = gt::sg::gate_rest(c->d_cam, n_pix, net, pg, tau, band, axis, dir_tol, t, r, th, ph,
+                           status, nsteps, list, d_count, c->stream);
+    if (rc == GT_OK) rc = list_count(&n2);
+    if (rc == GT_OK && n2 > 0)
+        rc = run_trace(c, c->d_cam, 1, kind, 0, n2, n_steps, sp, mode, t, r, th, ph, status,
+                       nsteps, list, nullptr);
     if (rc != GT_OK) return rc;
-    unsigned long long nfb = 0;
-    err = cudaMemcpyAsync(&nfb, d_nfb, sizeof nfb, cudaMemcpyDeviceToHost, c->stream);
-    if (err == cudaSuccess) err = cudaStreamSynchronize(c->stream);
-    if (err != cudaSuccess) return cuda_code(err);
-    if (n_fallback) *n_fallback = (int64_t)nfb;
-    if (nfb == 0) return GT_OK;
-    return run_trace(c, c->d_cam, 1, kind, 0, (int64_t)nfb, n_steps, sp, mode, t, r, th, ph,
-                     status, nsteps, c->d_fallback, nullptr);
+    if (n_fallback) *n_fallback = n1 - np + n2;
+    if (n_probes) *n_probes = np;
+    return GT_OK;
 }
 
 int gt_autotune(gt_ctx *c, int mode, int64_t trial_rays, int64_t trial_steps, double sp,
@@ -1064,17 +1083,19 @@ int gt_sync(gt_ctx *c)
     return cuda_code(cudaStreamSynchronize(c->stream));
 }
 
-int gt_get_stats(gt_ctx *c, int64_t *zone_steps)
+int gt_get_stats(gt_ctx *c, int64_t *zone_steps, int64_t *zone_f64_evals)
 {
     if (!c || !zone_steps) return GT_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     if (!g.ok) return GT_ERR_CUDA;
-    unsigned long long v = 0;
-    cudaError_t e = cudaMemcpyAsync(&v, c->d_scratch + gt::SCR_ZONE_STEPS, sizeof v,
+    unsigned long long v[2] = {0, 0}; // SCR_ZONE_STEPS, SCR_ZONE_F64 (adjacent words)
+    static_assert(gt::SCR_ZONE_F64 == gt::SCR_ZONE_STEPS + 1, "zone words are adjacent");
+    cudaError_t e = cudaMemcpyAsync(v, c->d_scratch + gt::SCR_ZONE_STEPS, sizeof v,
                                     cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_code(e);
-    *zone_steps = (int64_t)v;
+    *zone_steps = (int64_t)v[0];
+    if (zone_f64_evals) *zone_f64_evals = (int64_t)v[1];
     return GT_OK;
 }
 

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include "../../include/geotrace.h"
+#include "df.cuh"
 #include "spacetime.cuh"
 
 // The context's stream (capi.cu).
@@ -28,7 +29,8 @@ struct CamDesc {
     double inv_sin_th0;     // 1/sin(theta0), or 1 with GT_FLAG_COMPAT_CAMERA
     double gl_tt, gl_tph, gl_phph, gl_rr, gl_thth; // lower metric at the camera
     double r_escape;        // 1.5 r0
-    double r_switch;        // FP32-mixed: FP64 zone radius
+    double r_switch;        // FP32-mixed: zone radius
+    SpacetimeT<DF> st_df;   // the spacetime constants in double-float (the zone's field)
     int32_t valid;          // 1 when the camera sits where g_tt < 0
     int32_t pad_;
 };
@@ -39,8 +41,9 @@ enum : int {
     SCR_TIMEOUT = 1,    // set to 1 by the watchdog
     SCR_TO64 = 2,       // FP32-mixed: rays parked for the FP64 zone kernel
     SCR_TO32 = 3,       // FP32-mixed: rays handed back to the FP32 kernel
-    SCR_ZONE_STEPS = 4, // FP32-mixed: RK4 steps taken in the FP64 zone (gt_get_stats)
-    SCR_WORDS = 5
+    SCR_ZONE_STEPS = 4, // FP32-mixed: RK4 steps taken in the zone (gt_get_stats)
+    SCR_ZONE_F64 = 5,   // FP32-mixed: zone field evaluations done in FP64 (gt_get_stats)
+    SCR_WORDS = 6
 };
 
 // Kernel modes (public GT_MODE_FP32_MIXED runs MIXED_FP32 and ZONE_FP64 in rounds).
@@ -101,6 +104,7 @@ struct TraceArgs {
     // float copies for the FP32 kernel, filled by launch_trace (kernel parameters the
     // loop reads directly, so no per-step conversions are rematerialised)
     float sp_f, w6_f, h_thr_f;
+    DF sp_df, w6_df; // double-float copies for the zone
     int flags;
     int reproject_every;
     uint64_t timeout_ns; // 0 = no watchdog
@@ -115,6 +119,7 @@ struct TraceArgs {
     double *z;        // redshift factor per ray (ring hits; NaN otherwise) or null
     StateArrays states; // with states.t != null fresh rays start from these arrays and the
                         // end states (all 8 components) are written back to them
+    int zone_df;        // FP32-mixed: the zone's Manko-Novikov field in double-float
 };
 
 // Host-side validation shared by every entry point that takes a spacetime or a camera

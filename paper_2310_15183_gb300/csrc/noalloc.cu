@@ -141,12 +141,13 @@ extern "C" int gt_trace_batch_noalloc(int device, void *cuda_stream, const gt_ca
     a.status = status;
     a.nsteps = nsteps;
     a.scratch = words;
+    a.zone_df = 1; // the context's default zone (double-float Manko-Novikov field)
     const int kind = any_mn && any_kerr ? 2 : (any_mn ? gt::KIND_MN : gt::KIND_KERR);
     const int block = 128;
     const int fit = gt::max_blocks_per_sm(
         mode == GT_MODE_FP64 ? gt::KMODE_FP64 : gt::KMODE_MIXED_INLINE, kind, block);
     const int grid = (fit < 4 ? fit : 4) * sms;
-    // FP32-mixed runs its FP64 zone inline here: the park lists of the context path
+    // FP32-mixed runs its zone inline here: the park lists of the context path
     // would need allocated memory
     e = gt::launch_trace(a, mode == GT_MODE_FP64 ? gt::KMODE_FP64 : gt::KMODE_MIXED_INLINE, kind,
                          block, grid, false, s);

@@ -317,9 +317,11 @@ GT_HD void mn_potentials(const SpacetimeT<T> &c, T r, T th, MNPot<N> &P)
 // rounding like the dual-number form below (mn_rates_fwd), with less than half its
 // arithmetic: a product costs one multiply forward and two fused multiply-adds backward
 // instead of five operations for a value and two derivatives.
+// ex (optional) receives the four exponents of the evaluation, -2 beta Ea, 2 beta Eb,
+// 2 psi and 2 psi - 2 gamma'': the double-float evaluation checks its range with them.
 template <class T, bool TAIL = false>
 GT_HD void mn_rates_sc(const SpacetimeT<T> &c, T r, T s, T cs, T pr, T pth, T pt, T pph,
-                       Rates<T> &o)
+                       Rates<T> &o, T *ex = nullptr)
 {
     // ---- forward sweep (values)
     const T ik = T(c.ik), tb = T(c.two_beta), al = T(c.alpha);
@@ -389,8 +391,9 @@ GT_HD void mn_rates_sc(const SpacetimeT<T> &c, T r, T s, T cs, T pr, T pth, T pt
         Eb = xpy * T2 + T(1);
         Eg = T(2) * (x * iRP - y * uR2) - T(2);
     }
-    const T fa = exp_t(Ea * (-tb)) * (-al);
-    const T fb = exp_t(Eb * tb) * al;
+    const T xa = Ea * (-tb), xb = Eb * tb;
+    const T fa = exp_t(xa) * (-al);
+    const T fb = exp_t(xb) * al;
     const T ab = fa * fb;
     const T opab = ab + T(1);
     const T bma = fb - fa;
@@ -423,7 +426,14 @@ GT_HD void mn_rates_sc(const SpacetimeT<T> &c, T r, T s, T cs, T pr, T pth, T pt
     const T ieC = ie2psi * C;
     const T om0 = ieC * iA;
     const T om = om0 * T(c.two_k) - T(c.w_inf);
-    const T eG = exp_t(psi2 - g2);
+    const T xg = psi2 - g2;
+    const T eG = exp_t(xg);
+    if (ex) {
+        ex[0] = xa;
+        ex[1] = xb;
+        ex[2] = psi2;
+        ex[3] = xg;
+    }
     const T iBc = iB * T(c.c_g);
     const T G = eG * iBc;
     const T Delta = x2m1 * T(c.k2);

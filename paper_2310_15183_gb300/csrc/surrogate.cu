@@ -320,138 +320,186 @@ __device__ __forceinline__ bool is_probe(int i, int j, const ProbeGrid &pg, int 
     return (i % pg.stride == 0 || i == res_x - 1) && (j % pg.stride == 0 || j == res_y - 1);
 }
 
-__global__ void probe_pixels_kernel(const CamDesc *cam, ProbeGrid pg, int64_t *pix)
+// The network's answer per pixel (logit, direction) kept for the passes below.
+__global__ void net_out_kernel(int64_t n, int64_t pix0, const float *Z5, float4 *net)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float *z = Z5 + k * 16;
+    net[pix0 + k] = make_float4(z[0], z[1], z[2], z[3]);
+}
+
+// Gates that send a pixel to the integrator whatever the probes say: an unsure logit, the
+// Kerr photon-ring band, the axis, an unsettled direction length.
+__device__ __forceinline__ bool pixel_gates(const CamDesc &cam, int64_t pix, float4 z, float tau,
+                                            double band, double axis, float dir_tol)
+{
+    if (fabsf(z.x) < tau) return true;
+    if ((band > 0.0 && cam.st.kind == KIND_KERR) || axis > 0.0) {
+        Ray64 p;
+        camera_init(cam, pix, p);
+        if (band > 0.0 && cam.st.kind == KIND_KERR && fabs(kerr_rmin(cam, p)) < band) return true;
+        if (axis > 0.0 && kerr_min_sin2(cam, p) < axis * axis) return true;
+    }
+    if (dir_tol > 0.0f && z.x > 0.0f) {
+        const float nn = sqrtf(z.y * z.y + z.z * z.z + z.w * z.w);
+        if (!(fabsf(nn - 1.0f) <= dir_tol)) return true;
+    }
+    return false;
+}
+
+// The probe cell holding pixel (i, j): corner columns x0 < x1 and rows y0 < y1, and the
+// index (kx, ky) of its upper-left probe.
+struct Cell {
+    int kx, ky, x0, x1, y0, y1;
+};
+
+__device__ __forceinline__ Cell cell_of(int i, int j, const ProbeGrid &pg, int res_x, int res_y)
+{
+    Cell c;
+    c.kx = min(i / pg.stride, pg.nx - 2);
+    c.ky = min(j / pg.stride, pg.ny - 2);
+    c.x0 = probe_coord(c.kx, pg.stride, pg.nx, res_x);
+    c.x1 = probe_coord(c.kx + 1, pg.stride, pg.nx, res_x);
+    c.y0 = probe_coord(c.ky, pg.stride, pg.ny, res_y);
+    c.y1 = probe_coord(c.ky + 1, pg.stride, pg.ny, res_y);
+    return c;
+}
+
+// First integrator list: the probes, every pixel a gate sends to the integrator, and --
+// with probes -- every pixel whose predicted escape differs from the network's prediction
+// at one of its cell's corners (such a pixel fails the cell test whatever the integrator
+// finds at the corners).  Tracing them in the probes' launch leaves one tail of long rays
+// where two passes would leave two.
+__device__ __forceinline__ bool first_pass_pixel(const CamDesc &cam, const float4 *net, int64_t pix,
+                                                 const ProbeGrid &pg, float tau, double band,
+                                                 double axis, float dir_tol)
+{
+    const int res_x = cam.res_x, res_y = cam.res_y;
+    const int i = (int)(pix % res_x), j = (int)(pix / res_x);
+    const float4 z = net[pix];
+    if (pg.stride > 0) {
+        if (is_probe(i, j, pg, res_x, res_y)) return true;
+        const Cell c = cell_of(i, j, pg, res_x, res_y);
+        const bool esc = z.x > 0.0f;
+        const int64_t r0 = (int64_t)c.y0 * res_x, r1 = (int64_t)c.y1 * res_x;
+        if ((net[r0 + c.x0].x > 0.0f) != esc || (net[r0 + c.x1].x > 0.0f) != esc ||
+            (net[r1 + c.x0].x > 0.0f) != esc || (net[r1 + c.x1].x > 0.0f) != esc)
+            return true;
+    }
+    return pixel_gates(cam, pix, z, tau, band, axis, dir_tol);
+}
+
+// warp-aggregated append of the flagged pixels to a list
+__device__ __forceinline__ void append_flagged(bool flag, int64_t pix, int64_t *list,
+                                               unsigned long long *count)
+{
+    const unsigned mask = __ballot_sync(0xffffffffu, flag);
+    if (mask) {
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(mask) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(mask));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (flag) list[base + __popc(mask & ((1u << lane) - 1u))] = pix;
+    }
+}
+
+__global__ void select_kernel(int64_t n_pix, const CamDesc *cam, const float4 *net, ProbeGrid pg,
+                              float tau, double band, double axis, float dir_tol, int64_t *list,
+                              unsigned long long *count)
+{
+    const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool flag = pix < n_pix && first_pass_pixel(*cam, net, pix, pg, tau, band, axis, dir_tol);
+    append_flagged(flag, pix, list, count);
+}
+
+// Probe records from the integrator's results (already in the image) and the network's
+// answers at the probes.
+__global__ void probe_record_kernel(const CamDesc *cam, ProbeGrid pg, const float4 *net,
+                                    const uint8_t *status, const double *th, const double *ph,
+                                    ProbeRec *rec)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= pg.nx * pg.ny) return;
     const int kx = k % pg.nx, ky = k / pg.nx;
-    const int i = probe_coord(kx, pg.stride, pg.nx, cam->res_x);
-    const int j = probe_coord(ky, pg.stride, pg.ny, cam->res_y);
-    pix[k] = (int64_t)j * cam->res_x + i;
-}
-
-// Probe records from the integrator's results and the network's outputs on the probes.
-__global__ void probe_record_kernel(int n, const float *Z5, const uint8_t *st, const double *th,
-                                    const double *ph, ProbeRec *rec)
-{
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const float *z = Z5 + (int64_t)k * 16;
+    const int64_t pix = (int64_t)probe_coord(ky, pg.stride, pg.ny, cam->res_y) * cam->res_x +
+                        probe_coord(kx, pg.stride, pg.nx, cam->res_x);
+    const float4 z = net[pix];
     ProbeRec o;
-    o.exact = st[k];
-    o.net_esc = z[0] > 0.0f ? 1 : 0;
+    o.exact = status[pix];
+    o.net_esc = z.x > 0.0f ? 1 : 0;
     o.pad[0] = o.pad[1] = 0;
-    if (st[k] == GT_RAY_ESCAPED) {
-        const double s = sin(th[k]);
-        o.err[0] = (float)(s * cos(ph[k])) - z[1];
-        o.err[1] = (float)(s * sin(ph[k])) - z[2];
-        o.err[2] = (float)cos(th[k]) - z[3];
+    if (o.exact == GT_RAY_ESCAPED) {
+        const double s = sin(th[pix]);
+        o.err[0] = (float)(s * cos(ph[pix])) - z.y;
+        o.err[1] = (float)(s * sin(ph[pix])) - z.z;
+        o.err[2] = (float)cos(th[pix]) - z.w;
     } else {
         o.err[0] = o.err[1] = o.err[2] = 0.0f;
     }
     rec[k] = o;
 }
 
-// The probes' exact results into the image (their pixels are neither network nor fallback).
-__global__ void scatter_probes_kernel(int n, const int64_t *pix, const double *pt, const double *pr,
-                                      const double *pth, const double *pph, const uint8_t *pst,
-                                      const uint32_t *pns, double *t, double *r, double *th,
-                                      double *ph, uint8_t *status, uint32_t *nsteps)
-{
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const int64_t q = pix[k];
-    t[q] = pt[k];
-    r[q] = pr[k];
-    th[q] = pth[k];
-    ph[q] = pph[k];
-    status[q] = pst[k];
-    nsteps[q] = pns[k];
-}
-
-// Decide per pixel: confident surrogate answer, or fall back to the integrator.  With
-// probes, a pixel is taken from the network only inside a probe cell whose four corners
-// the integrator and the network classify alike -- all escaped, or all not escaping with
-// one common end (all HORIZON, or all MAXSTEPS: trapped; the pixel takes that status) --
-// and, for escaped ones, whose corner error vectors differ by less than pg.tol; its end direction is the network's plus the bilinear interpolation of the
-// corners' error vectors (the integrator correcting the network where it measured it).
-__global__ void gate_kernel(int64_t n, int64_t pix0, const CamDesc *cam, const float *Z5, float tau,
-                            double band, double axis, float dir_tol, ProbeGrid pg, double *t, double *r,
-                            double *th, double *ph, uint8_t *status, uint32_t *nsteps,
+// Every pixel the first pass did not trace: with probes, taken from the network only
+// inside a probe cell whose four corners the integrator and the network classify alike --
+// all escaped, or all not escaping with one common end (all HORIZON, or all MAXSTEPS:
+// trapped; the pixel takes that status) -- and, for escaped ones, whose corner error
+// vectors differ by less than pg.tol; its end direction is the network's plus the bilinear
+// interpolation of the corners' error vectors (the integrator correcting the network
+// where it measured it).  The rest go to the second integrator list.
+__global__ void gate_kernel(int64_t n_pix, const CamDesc *cam, const float4 *net, ProbeGrid pg,
+                            float tau, double band, double axis, float dir_tol, double *t,
+                            double *r, double *th, double *ph, uint8_t *status, uint32_t *nsteps,
                             int64_t *fallback, unsigned long long *n_fallback)
 {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool fb = false;
-    int64_t pix = pix0 + k;
-    if (k < n) {
+    if (pix < n_pix && !first_pass_pixel(*cam, net, pix, pg, tau, band, axis, dir_tol)) {
         const int res_x = cam->res_x, res_y = cam->res_y;
         const int i = (int)(pix % res_x), j = (int)(pix / res_x);
-        const float *z = Z5 + k * 16;
-        const float logit = z[0];
-        float nx = z[1], ny = z[2], nz = z[3];
-        bool skip = false; // a probe: written by the integrator pass
+        const float4 z = net[pix];
+        float nx = z.y, ny = z.z, nz = z.w;
         int cap_status = GT_RAY_HORIZON; // status given to a captured network pixel
         if (pg.stride > 0) {
-            if (is_probe(i, j, pg, res_x, res_y)) {
-                skip = true;
-            } else {
-                const int kx = min(i / pg.stride, pg.nx - 2), ky = min(j / pg.stride, pg.ny - 2);
-                const int x0 = probe_coord(kx, pg.stride, pg.nx, res_x);
-                const int x1 = probe_coord(kx + 1, pg.stride, pg.nx, res_x);
-                const int y0 = probe_coord(ky, pg.stride, pg.ny, res_y);
-                const int y1 = probe_coord(ky + 1, pg.stride, pg.ny, res_y);
-                const ProbeRec &c00 = pg.rec[ky * pg.nx + kx], &c01 = pg.rec[ky * pg.nx + kx + 1];
-                const ProbeRec &c10 = pg.rec[(ky + 1) * pg.nx + kx];
-                const ProbeRec &c11 = pg.rec[(ky + 1) * pg.nx + kx + 1];
-                const bool esc4 = c00.exact == GT_RAY_ESCAPED && c01.exact == GT_RAY_ESCAPED &&
-                                  c10.exact == GT_RAY_ESCAPED && c11.exact == GT_RAY_ESCAPED &&
-                                  c00.net_esc && c01.net_esc && c10.net_esc && c11.net_esc;
-                // not escaping: the four corners end alike (all HORIZON, or all still
-                // bound at the step cap -- MAXSTEPS, the trapped rays of Manko-Novikov)
-                const bool cap4 = (c00.exact == GT_RAY_HORIZON || c00.exact == GT_RAY_MAXSTEPS) &&
-                                  c01.exact == c00.exact && c10.exact == c00.exact &&
-                                  c11.exact == c00.exact && !c00.net_esc && !c01.net_esc &&
-                                  !c10.net_esc && !c11.net_esc;
-                cap_status = c00.exact;
-                if (logit > 0.0f) {
-                    float sp = 0.0f, sq = 0.0f;
+            const Cell cl = cell_of(i, j, pg, res_x, res_y);
+            const int kx = cl.kx, ky = cl.ky, x0 = cl.x0, x1 = cl.x1, y0 = cl.y0, y1 = cl.y1;
+            const ProbeRec &c00 = pg.rec[ky * pg.nx + kx], &c01 = pg.rec[ky * pg.nx + kx + 1];
+            const ProbeRec &c10 = pg.rec[(ky + 1) * pg.nx + kx];
+            const ProbeRec &c11 = pg.rec[(ky + 1) * pg.nx + kx + 1];
+            const bool esc4 = c00.exact == GT_RAY_ESCAPED && c01.exact == GT_RAY_ESCAPED &&
+                              c10.exact == GT_RAY_ESCAPED && c11.exact == GT_RAY_ESCAPED &&
+                              c00.net_esc && c01.net_esc && c10.net_esc && c11.net_esc;
+            const bool cap4 = (c00.exact == GT_RAY_HORIZON || c00.exact == GT_RAY_MAXSTEPS) &&
+                              c01.exact == c00.exact && c10.exact == c00.exact &&
+                              c11.exact == c00.exact && !c00.net_esc && !c01.net_esc &&
+                              !c10.net_esc && !c11.net_esc;
+            cap_status = c00.exact;
+            if (z.x > 0.0f) {
+                float sp = 0.0f, sq = 0.0f;
 #pragma unroll
-                    for (int m = 0; m < 3; m++) {
-                        const float a = c00.err[m] - c11.err[m], b = c01.err[m] - c10.err[m];
-                        sp = fmaf(a, a, sp);
-                        sq = fmaf(b, b, sq);
-                    }
-                    if (!esc4 || !(fmaxf(sp, sq) < pg.tol * pg.tol)) {
-                        fb = true;
-                    } else {
-                        const float tx = (float)(i - x0) / (float)(x1 - x0);
-                        const float ty = (float)(j - y0) / (float)(y1 - y0);
-                        const float w00 = (1.0f - tx) * (1.0f - ty), w01 = tx * (1.0f - ty);
-                        const float w10 = (1.0f - tx) * ty, w11 = tx * ty;
-                        nx += w00 * c00.err[0] + w01 * c01.err[0] + w10 * c10.err[0] + w11 * c11.err[0];
-                        ny += w00 * c00.err[1] + w01 * c01.err[1] + w10 * c10.err[1] + w11 * c11.err[1];
-                        nz += w00 * c00.err[2] + w01 * c01.err[2] + w10 * c10.err[2] + w11 * c11.err[2];
-                    }
-                } else if (!cap4) {
-                    fb = true;
+                for (int m = 0; m < 3; m++) {
+                    const float a = c00.err[m] - c11.err[m], b = c01.err[m] - c10.err[m];
+                    sp = fmaf(a, a, sp);
+                    sq = fmaf(b, b, sq);
                 }
+                if (!esc4 || !(fmaxf(sp, sq) < pg.tol * pg.tol)) {
+                    fb = true;
+                } else {
+                    const float tx = (float)(i - x0) / (float)(x1 - x0);
+                    const float ty = (float)(j - y0) / (float)(y1 - y0);
+                    const float w00 = (1.0f - tx) * (1.0f - ty), w01 = tx * (1.0f - ty);
+                    const float w10 = (1.0f - tx) * ty, w11 = tx * ty;
+                    nx += w00 * c00.err[0] + w01 * c01.err[0] + w10 * c10.err[0] + w11 * c11.err[0];
+                    ny += w00 * c00.err[1] + w01 * c01.err[1] + w10 * c10.err[1] + w11 * c11.err[1];
+                    nz += w00 * c00.err[2] + w01 * c01.err[2] + w10 * c10.err[2] + w11 * c11.err[2];
+                }
+            } else if (!cap4) {
+                fb = true;
             }
         }
-        if (!skip && !fb) {
-            bool ring = false;
-            if ((band > 0.0 && cam->st.kind == KIND_KERR) || axis > 0.0) {
-                Ray64 p;
-                camera_init(*cam, pix, p);
-                if (band > 0.0 && cam->st.kind == KIND_KERR) ring = fabs(kerr_rmin(*cam, p)) < band;
-                if (axis > 0.0) ring = ring || kerr_min_sin2(*cam, p) < axis * axis;
-            }
-            const float nn = sqrtf(z[1] * z[1] + z[2] * z[2] + z[3] * z[3]);
-            // an escaping prediction whose direction vector is not of unit length is unsettled
-            const bool loose = dir_tol > 0.0f && logit > 0.0f && !(fabsf(nn - 1.0f) <= dir_tol);
-            fb = fabsf(logit) < tau || ring || loose;
-        }
-        if (!skip && !fb) {
-            if (logit > 0.0f) {
+        if (!fb) {
+            if (z.x > 0.0f) {
                 const float nc = sqrtf(nx * nx + ny * ny + nz * nz);
                 th[pix] = acos(fminf(fmaxf(nz / nc, -1.0f), 1.0f));
                 ph[pix] = atan2(ny, nx);
@@ -466,16 +514,7 @@ __global__ void gate_kernel(int64_t n, int64_t pix0, const CamDesc *cam, const f
             nsteps[pix] = 0;
         }
     }
-    // warp-aggregated append of the fallback pixels
-    const unsigned mask = __ballot_sync(0xffffffffu, fb);
-    if (mask) {
-        const int lane = threadIdx.x & 31;
-        const int leader = __ffs(mask) - 1;
-        unsigned long long base = 0;
-        if (lane == leader) base = atomicAdd(n_fallback, (unsigned long long)__popc(mask));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (fb) fallback[base + __popc(mask & ((1u << lane) - 1u))] = pix;
-    }
+    append_flagged(fb, pix, fallback, n_fallback);
 }
 
 } // namespace sg
@@ -940,10 +979,8 @@ int gt_surrogate_train(gt_ctx *ctx, gt_surrogate *s, const gt_train_cfg *cfg, in
 namespace gt {
 namespace sg {
 
-int infer_chunks(gt_surrogate *s, const CamDesc *d_cam, int64_t n_pix, float tau, double band,
-                 double axis, float dir_tol, const ProbeGrid &pg, double *t, double *r, double *th, double *ph,
-                 uint8_t *status, uint32_t *nsteps, int64_t *d_fallback, unsigned long long *d_nfb,
-                 cudaStream_t st)
+// The network on every pixel of the camera; its answers to `net` (float4 per pixel).
+int net_pass(gt_surrogate *s, const CamDesc *d_cam, int64_t n_pix, float4 *net, cudaStream_t st)
 {
     const int64_t chunk = 1 << 19;
     int rc = ensure_ws(s, n_pix < chunk ? n_pix : chunk);
@@ -951,44 +988,39 @@ int infer_chunks(gt_surrogate *s, const CamDesc *d_cam, int64_t n_pix, float tau
     for (int64_t p0 = 0; p0 < n_pix; p0 += chunk) {
         const int64_t B = n_pix - p0 < chunk ? n_pix - p0 : chunk;
         camera_features_kernel<<<blocks_for(B), 256, 0, st>>>(B, p0, d_cam, s->norm, s->X[0]);
-        cudaError_t e = forward(s, (int)B, st, false);
-        if (e != cudaSuccess) return GT_ERR_CUDA;
-        gate_kernel<<<blocks_for(B), 256, 0, st>>>(B, p0, d_cam, s->Z[N_LAYERS - 1], tau, band,
-                                                   axis, dir_tol, pg, t, r, th, ph, status, nsteps,
-                                                   d_fallback, d_nfb);
+        if (forward(s, (int)B, st, false) != cudaSuccess) return GT_ERR_CUDA;
+        net_out_kernel<<<blocks_for(B), 256, 0, st>>>(B, p0, s->Z[N_LAYERS - 1], net);
         if (cudaGetLastError() != cudaSuccess) return GT_ERR_CUDA;
     }
     return check_err(s, st);
 }
 
-int probe_pixels(const CamDesc *d_cam, const ProbeGrid &pg, int64_t *d_pix, cudaStream_t st)
+int select_first(const CamDesc *d_cam, int64_t n_pix, const float4 *net, const ProbeGrid &pg,
+                 float tau, double band, double axis, float dir_tol, int64_t *list,
+                 unsigned long long *count, cudaStream_t st)
 {
-    const int n = pg.nx * pg.ny;
-    probe_pixels_kernel<<<blocks_for(n), 256, 0, st>>>(d_cam, pg, d_pix);
+    select_kernel<<<blocks_for(n_pix), 256, 0, st>>>(n_pix, d_cam, net, pg, tau, band, axis,
+                                                     dir_tol, list, count);
     return cudaGetLastError() == cudaSuccess ? GT_OK : GT_ERR_CUDA;
 }
 
-// The network on the probe pixels, the probe records, and the probes' exact results
-// written into the image.
-int probe_records(gt_surrogate *s, const CamDesc *d_cam, const int64_t *d_pix, int n,
-                  const double *pt, const double *pr, const double *pth, const double *pph,
-                  const uint8_t *pst, const uint32_t *pns, ProbeRec *rec, double *t, double *r,
-                  double *th, double *ph, uint8_t *status, uint32_t *nsteps, cudaStream_t st)
+int probe_records(const CamDesc *d_cam, const ProbeGrid &pg, const float4 *net,
+                  const uint8_t *status, const double *th, const double *ph, ProbeRec *rec,
+                  cudaStream_t st)
 {
-    const int64_t chunk = 1 << 19;
-    int rc = ensure_ws(s, n < chunk ? n : chunk);
-    if (rc != GT_OK) return rc;
-    for (int64_t p0 = 0; p0 < n; p0 += chunk) {
-        const int64_t B = n - p0 < chunk ? n - p0 : chunk;
-        camera_features_kernel<<<blocks_for(B), 256, 0, st>>>(B, p0, d_cam, s->norm, s->X[0], d_pix);
-        if (forward(s, (int)B, st, false) != cudaSuccess) return GT_ERR_CUDA;
-        probe_record_kernel<<<blocks_for(B), 256, 0, st>>>((int)B, s->Z[N_LAYERS - 1], pst + p0,
-                                                           pth + p0, pph + p0, rec + p0);
-    }
-    scatter_probes_kernel<<<blocks_for(n), 256, 0, st>>>(n, d_pix, pt, pr, pth, pph, pst, pns, t, r,
-                                                         th, ph, status, nsteps);
-    if (cudaGetLastError() != cudaSuccess) return GT_ERR_CUDA;
-    return check_err(s, st);
+    const int n = pg.nx * pg.ny;
+    probe_record_kernel<<<blocks_for(n), 256, 0, st>>>(d_cam, pg, net, status, th, ph, rec);
+    return cudaGetLastError() == cudaSuccess ? GT_OK : GT_ERR_CUDA;
+}
+
+int gate_rest(const CamDesc *d_cam, int64_t n_pix, const float4 *net, const ProbeGrid &pg,
+              float tau, double band, double axis, float dir_tol, double *t, double *r, double *th,
+              double *ph, uint8_t *status, uint32_t *nsteps, int64_t *list,
+              unsigned long long *count, cudaStream_t st)
+{
+    gate_kernel<<<blocks_for(n_pix), 256, 0, st>>>(n_pix, d_cam, net, pg, tau, band, axis, dir_tol,
+                                                   t, r, th, ph, status, nsteps, list, count);
+    return cudaGetLastError() == cudaSuccess ? GT_OK : GT_ERR_CUDA;
 }
 
 } // namespace sg

@@ -26,6 +26,7 @@
 #include "compensated.cuh"
 #include "internal.cuh"
 #include "spacetime.cuh"
+#include "zone_df.cuh"
 
 namespace gt {
 
@@ -70,6 +71,7 @@ __device__ void setup_desc(CamDesc &d, int flags, double r_switch)
         st.r_plus = d.M + sqrt(d.M * d.M - st.a2);
     }
     d.st = st;
+    d.st_df = to_df(st);
     d.V = tan(0.5 * d.fov_deg / 180.0 * M_PI) / d.r0;
     d.H = atan(tan(d.V) * (double)d.res_x / (double)d.res_y);
     d.inv_sin_th0 = (flags & GT_FLAG_COMPAT_CAMERA) ? 1.0 : 1.0 / sin(d.th0);
@@ -244,6 +246,97 @@ __device__ __forceinline__ double step64(const TraceArgs &A, const SpacetimeC &s
 {
     if (A.euler) return euler_step64<KIND>(st, x, A.sp, y);
     return rk4_step64<KIND>(st, x, A.sp, A.w6, y);
+}
+
+// ------------------------------------------------------------------ the zone in double-float
+// The FP32-mixed path's zone steps an FP64 state.  Within a step the stage arithmetic --
+// the stage points, the sin/cos rotation, the Manko-Novikov field, the stage sums and
+// the step length -- runs in double-float (zone_df.cuh) on the FP32 pipes; the state is
+// converted once into double-float at the start of the step, the increments once back,
+// and added in FP64.  A field evaluation outside the double-float range (and Kerr, which
+// has no zone by default) takes FP64; n_f64 counts those evaluations.
+template <int KIND>
+__device__ __forceinline__ void zone_rates(const SpacetimeC &st, const SpacetimeT<DF> *sd, DF r,
+                                           DF s, DF cs, DF pr, DF pth, DF pt, DF pph,
+                                           Rates<DF> &o, uint32_t &n_f64)
+{
+    const bool mn = KIND == KIND_MN || (KIND == KIND_ANY && st.kind == KIND_MN);
+    if (mn && mn_rates_df(*sd, r, s, cs, pr, pth, pt, pph, o)) return;
+    ++n_f64;
+    Rates<double> o64;
+    rates_any<KIND>(st, df_to(r), df_to(s), df_to(cs), df_to(pr), df_to(pth), df_to(pt),
+                    df_to(pph), o64);
+    o.dt = DF(o64.dt);
+    o.dr = DF(o64.dr);
+    o.dth = DF(o64.dth);
+    o.dph = DF(o64.dph);
+    o.dpr = DF(o64.dpr);
+    o.dpth = DF(o64.dpth);
+}
+
+__device__ __forceinline__ DF df_twice(DF a) { return DF(2.0f * a.hi, 2.0f * a.lo); }
+
+// One RK4 step of the zone: the stages of rk4_step64 (stage points x + h/2 k1, x + h/2 k2,
+// x + h k3; weights 1, 2, 2, 1 times h w6; h = |sp / k1.dt|) in a rolled stage loop, so one
+// copy of the double-float field is compiled.  sd: the spacetime constants in
+// double-float; sp_df, w6_df: step precision and RK4 weight in double-float.
+template <int KIND>
+__device__ __forceinline__ double rk4_step_zone(const SpacetimeC &st, const SpacetimeT<DF> *sd,
+                                                const Ray64 &x, DF sp_df, DF w6_df, Ray64 &y,
+                                                uint32_t &n_f64)
+{
+    double s64, c64;
+    sincos(x.th, &s64, &c64);
+    const DF S1(s64), C1(c64), R0(x.r), PR0(x.pr), PTH0(x.pth), PT(x.pt), PPH(x.pph);
+    Rates<DF> k, acc;
+    DF h(0.0f, 0.0f), r = R0, pr = PR0, pth = PTH0, s = S1, c = C1;
+#pragma unroll 1
+    for (int stage = 0; stage < 4; stage++) {
+        zone_rates<KIND>(st, sd, r, s, c, pr, pth, PT, PPH, k, n_f64);
+        if (stage == 0) {
+            h = sp_df * rcp_t(k.dt);
+            if (h.hi < 0.0f) h = -h;
+            acc = k;
+        } else if (stage < 3) {
+            acc.dt = acc.dt + df_twice(k.dt);
+            acc.dr = acc.dr + df_twice(k.dr);
+            acc.dth = acc.dth + df_twice(k.dth);
+            acc.dph = acc.dph + df_twice(k.dph);
+            acc.dpr = acc.dpr + df_twice(k.dpr);
+            acc.dpth = acc.dpth + df_twice(k.dpth);
+        } else {
+            acc.dt = acc.dt + k.dt;
+            acc.dr = acc.dr + k.dr;
+            acc.dth = acc.dth + k.dth;
+            acc.dph = acc.dph + k.dph;
+            acc.dpr = acc.dpr + k.dpr;
+            acc.dpth = acc.dpth + k.dpth;
+        }
+        if (stage < 3) {
+            const DF d = stage < 2 ? DF(0.5f * h.hi, 0.5f * h.lo) : h;
+            r = R0 + d * k.dr;
+            pr = PR0 + d * k.dpr;
+            pth = PTH0 + d * k.dpth;
+            const DF dth = d * k.dth;
+            if (!rotate_sc_df(S1, C1, dth, &s, &c)) {
+                double s2, c2;
+                sincos(x.th + df_to(dth), &s2, &c2);
+                s = DF(s2);
+                c = DF(c2);
+            }
+        }
+    }
+    if (!isfinite(h.hi)) return nan("");
+    const DF hw = h * w6_df;
+    y.t = x.t + df_to(hw * acc.dt);
+    y.r = x.r + df_to(hw * acc.dr);
+    y.th = x.th + df_to(hw * acc.dth);
+    y.ph = x.ph + df_to(hw * acc.dph);
+    y.pr = x.pr + df_to(hw * acc.dpr);
+    y.pth = x.pth + df_to(hw * acc.dpth);
+    y.pt = x.pt;
+    y.pph = x.pph;
+    return df_to(h);
 }
 
 // ------------------------------------------------------------------ ring and redshift
@@ -529,6 +622,8 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A, int one_shot)
     bool drained = false;
     uint32_t n = 0;
     uint32_t n_entry = 0;           // step count when the ray entered this launch (zone steps)
+    uint32_t n_f64 = 0;             // zone field evaluations of the ray in FP64 (this launch)
+    SpacetimeT<DF> sd_ray;          // double-float constants of a per-ray spacetime
     uint32_t rp_next = 0xFFFFFFFFu; // next step count that is a multiple of reproject_every
     Ray64 x;
     RayMixed m;
@@ -566,6 +661,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A, int one_shot)
         d.offset = 0;
         setup_desc(d, A.flags, A.rays->r_switch);
         if (MODE != 2) st = d.st;
+        if (MODE == 1 || MODE == 3) sd_ray = d.st_df;
         r_esc = d.r_escape;
         r_sw = d.r_switch;
         if (MODE == 1 || MODE == 2) stf = to_float(d.st);
@@ -640,6 +736,7 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A, int one_shot)
             x.pph = it.pph;
         }
         n_entry = n;
+        n_f64 = 0;
         if (MODE == 1 || MODE == 2) {
             mixed_from64(x, m);
             if (A.reproject_every > 0) {
@@ -738,7 +835,14 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A, int one_shot)
         int status = -1;
         if (MODE == 0 || MODE == 3) {
             Ray64 y;
-            const double h = step64<KIND>(A, st, x, y);
+            double h;
+            if (MODE == 3 && A.zone_df) {
+                h = rk4_step_zone<KIND>(st, A.rays ? &sd_ray : &cams[cam].st_df, x, A.sp_df,
+                                        A.w6_df, y, n_f64);
+            } else {
+                h = step64<KIND>(A, st, x, y);
+                if (MODE == 3) n_f64 += 4;
+            }
             ++n;
             if (!isfinite(h) || !finite6(y)) {
                 status = GT_RAY_NONFINITE;
@@ -754,16 +858,23 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A, int one_shot)
                     if (ok) {
                         active = false;
                         atomicAdd(A.scratch + SCR_ZONE_STEPS, (unsigned long long)(n - n_entry));
+                        if (n_f64) atomicAdd(A.scratch + SCR_ZONE_F64, (unsigned long long)n_f64);
                     }
                 }
             }
         } else if (MODE == 1) {
             double h;
             bool ok = true;
-            if ((double)m.r.hi < r_sw) { // FP64 zone inline
+            if ((double)m.r.hi < r_sw) { // the zone inline
                 Ray64 y;
                 mixed_to64(m, x);
-                h = step64<KIND>(A, st, x, y);
+                if (A.zone_df) {
+                    h = rk4_step_zone<KIND>(st, A.rays ? &sd_ray : &cams[cam].st_df, x,
+                                            A.sp_df, A.w6_df, y, n_f64);
+                } else {
+                    h = step64<KIND>(A, st, x, y);
+                    n_f64 += 4;
+                }
                 ok = isfinite(h) && finite6(y);
                 if (ok) mixed_from64(y, m);
             } else {
@@ -843,7 +954,10 @@ __device__ __forceinline__ void trace_body(const TraceArgs &A, int one_shot)
             if (status >= 0) mixed_to64(m, x);
         }
         if (status >= 0) {
-            if (MODE == 3) atomicAdd(A.scratch + SCR_ZONE_STEPS, (unsigned long long)(n - n_entry));
+            if (MODE == 3) {
+                atomicAdd(A.scratch + SCR_ZONE_STEPS, (unsigned long long)(n - n_entry));
+                if (n_f64) atomicAdd(A.scratch + SCR_ZONE_F64, (unsigned long long)n_f64);
+            }
             double z = nan("");
             if (status == GT_RAY_DISK && A.z) z = redshift64<KIND>(cams[cam].st, cams[cam].gl_tt, x);
             store_full(A, id, x, status, n, z);
@@ -1032,6 +1146,8 @@ cudaError_t launch_trace_two(const TraceArgs &args, int kind_hint, int block, in
     a.sp_f = (float)a.sp;
     a.w6_f = (float)a.w6;
     a.h_thr_f = (float)(a.sp * 0.00003);
+    a.sp_df = DF(a.sp);
+    a.w6_df = DF(a.w6);
     return kind_hint == KIND_KERR ? launch_two<KIND_KERR>(a, block, grid, s)
                                   : launch_two<KIND_MN>(a, block, grid, s);
 }
@@ -1092,6 +1208,8 @@ cudaError_t launch_trace(const TraceArgs &args, int kmode, int kind_hint, int bl
     a.sp_f = (float)a.sp;
     a.w6_f = (float)a.w6;
     a.h_thr_f = (float)(a.sp * 0.00003);
+    a.sp_df = DF(a.sp);
+    a.w6_df = DF(a.w6);
     switch (kmode) {
     case KMODE_FP64: return launch_mode<0>(a, kind_hint, block, grid, one_shot, s);
     case KMODE_MIXED_INLINE: return launch_mode<1>(a, kind_hint, block, grid, one_shot, s);

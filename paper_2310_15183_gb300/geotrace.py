@@ -22,7 +22,7 @@ ERRORS = {-1: "invalid argument", -2: "not configured", -3: "CUDA error", -4: "o
 ESCAPED, HORIZON, MAXSTEPS, NONFINITE, TIMEOUT, DISK = 0, 1, 2, 3, 4, 5
 MODE_FP64, MODE_FP32_MIXED = 0, 1
 FLAG_COMPAT_WEIGHTS, FLAG_COMPAT_CAMERA, FLAG_ONE_SHOT, FLAG_GRAPH, FLAG_PRECISE_MN = 1, 2, 4, 8, 16
-FLAG_FD_DERIVS, FLAG_F32_IO, FLAG_EULER = 32, 64, 128
+FLAG_FD_DERIVS, FLAG_F32_IO, FLAG_EULER, FLAG_ZONE_FP64 = 32, 64, 128, 256
 # the listing's numerics: forward differences, float32 I/O, 0.1667 weights, v^phi = alpha
 FLAGS_PAPER = FLAG_FD_DERIVS | FLAG_F32_IO | FLAG_COMPAT_WEIGHTS | FLAG_COMPAT_CAMERA
 
@@ -103,7 +103,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.gt_trace_batch.argtypes = [vp, ctypes.POINTER(CameraDesc), i, i64, d, i] + out6
     lib.gt_sync.argtypes = [vp]
     lib.gt_device_sm_count.argtypes = [vp, ctypes.POINTER(i)]
-    lib.gt_get_stats.argtypes = [vp, ctypes.POINTER(i64)]
+    lib.gt_get_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
     lib.gt_measure_fma_peak.argtypes = [i, i, i, ctypes.POINTER(d)]
     lib.gt_gemm_bf16.argtypes = [i, vp, i, i, i, vp, i64, i64, vp, i64, i64, vp, i, vp, i64,
                                  i, i, i]
@@ -181,11 +181,17 @@ class Tracer:
         except Exception:
             pass
 
+    def zone_stats(self):
+        """(RK4 steps the last trace took in the zone, field evaluations of them done in
+        FP64) (gt_get_stats)."""
+        v, f = ctypes.c_int64(), ctypes.c_int64()
+        _check(self.lib.gt_get_stats(self.ctx, ctypes.byref(v), ctypes.byref(f)),
+               "gt_get_stats")
+        return v.value, f.value
+
     def zone_steps(self) -> int:
-        """RK4 steps the last trace took in the FP64 zone (gt_get_stats)."""
-        v = ctypes.c_int64()
-        _check(self.lib.gt_get_stats(self.ctx, ctypes.byref(v)), "gt_get_stats")
-        return v.value
+        """RK4 steps the last trace took in the zone (gt_get_stats)."""
+        return self.zone_stats()[0]
 
     def sm_count(self) -> int:
         n = ctypes.c_int()

@@ -69,6 +69,11 @@ WORKLOADS["mn512"] = Workload("mn512", dataclasses.replace(MN_1000, res_x=512, r
 WORKLOADS["mn256_short"] = Workload("mn256_short",
                                     dataclasses.replace(MN_1000, res_x=256, res_y=256),
                                     2000, 1.5e-4)
+# the camera inside the Manko-Novikov zone (r0 = 3.8M < 4M): every FP32-mixed ray is handed
+# to the zone kernel after its first step, so its launches carry the work
+WORKLOADS["mn256_zone"] = Workload("mn256_zone",
+                                   dataclasses.replace(MN_1000, r0=1.9, res_x=256, res_y=256),
+                                   4000, 1.5e-4)
 
 
 def sub_camera(cam: Camera, res_x: int, res_y: int) -> Camera:

@@ -76,3 +76,31 @@ def test_compensated_update_error_bound(tmp_path):
     for name, (ratio, lo) in res.items():
         assert ratio <= 1.0, (name, res)
         assert lo <= (1.0 if name == "zero_crossing" else 0.5), (name, res)
+
+
+def test_double_float_zone_arithmetic_and_rates(tmp_path):
+    """The double-float arithmetic of the FP32-mixed zone (csrc/df.cuh) against long double:
+    sum, sum under cancellation, product, reciprocal and inverse square root within a few
+    u^2 (u = 2^-24) of the result, exp within 2^-45 over [-69, 87], the stage rotation of
+    sin/cos within 4 u^2 for angles up to 1/16; and the Manko-Novikov
+    rates evaluated in double-float (zone_df.cuh) at random points of the zone of eight
+    spacetimes, where its range check accepts them, against long double: within ~64x the
+    error of the same evaluation in double at the median and the 99th percentile (the
+    ratio of the two precisions, 2^5), below 1e-6 of the largest rate everywhere, with the
+    range check accepting most of the zone and of the listing's trapped-ray shell."""
+    exe = str(tmp_path / "df_arith")
+    cuda_inc = os.path.join(os.path.dirname(os.path.dirname(build.nvcc())), "include")
+    subprocess.run(["g++", "-std=c++17", "-O1", "-ffp-contract=off", "-I" + cuda_inc,
+                    os.path.join(HERE, "df_arith.cpp"), "-o", exe], check=True)
+    res = json.loads(subprocess.run([exe], check=True, capture_output=True, text=True).stdout)
+    u2 = 2.0 ** -48
+    assert res["add"] <= 3 * u2 and res["add_cancel"] <= 3 * u2, res
+    assert res["mul"] <= 5 * u2, res
+    assert res["rcp"] <= 4 * u2 and res["rsqrt"] <= 6 * u2, res
+    assert res["exp"] <= 2.0 ** -45, res
+    assert res["rotate_abs"] <= 4 * u2 and res["rotate_refused"] == 0, res
+    assert res["zone_points_df"] >= 0.85 * res["zone_points"], res
+    assert res["shell_points_df"] >= 0.85 * res["shell_points"], res
+    assert res["rates_df_median"] <= 64 * res["rates_f64_median"], res
+    assert res["rates_df_p99"] <= 64 * res["rates_f64_p99"], res
+    assert res["rates_df_max"] < 1e-6, res

@@ -268,6 +268,28 @@ def test_mixed_terminating_classification_and_angle(tracer, oracle, cam, n_steps
     assert rep["agree"] >= 0.999 and rep["max_angle_escaped"] <= 1e-3, rep
 
 
+def test_mixed_zone_double_float_and_fp64(g, tracer, oracle):
+    """The FP32-mixed zone of Manko-Novikov with its field in double-float (the default)
+    and in FP64 (GT_FLAG_ZONE_FP64): both meet the mixed-precision criteria against the
+    oracle on terminating rays; the zone statistics count every zone evaluation as FP64
+    with the flag and a minority without it; and the two runs differ (the double-float
+    field ran)."""
+    cam = W.sub_camera(MN, 12, 10)
+    ref = run_oracle(oracle, cam, 500000, 1.5e-4, want_min_sin=True)
+    band = neighbour_band(ref["status"], cam.res_x, cam.res_y) | (ref["min_sin"] < 1e-3)
+    outs, stats = {}, {}
+    for name, flags in (("df", 0), ("f64", g.FLAG_ZONE_FP64)):
+        outs[name] = run_gpu(tracer, cam, 500000, 1.5e-4, mode=1, flags=flags)
+        stats[name] = tracer.zone_stats()
+        rep = mixed_report(outs[name], ref, exclude=band)
+        assert rep["agree"] >= 0.999 and rep["max_angle_escaped"] <= 1e-3, (name, rep)
+    steps, f64 = stats["f64"]
+    assert steps > 0 and f64 == 4 * steps, stats
+    steps_df, f64_df = stats["df"]
+    assert steps_df > 0 and f64_df < 0.5 * 4 * steps_df, stats
+    assert not np.array_equal(outs["df"]["th"], outs["f64"]["th"], equal_nan=True)
+
+
 def test_mixed_precise_mn_multipole_tails(g, tracer, oracle):
     """GT_FLAG_PRECISE_MN (closed-form multipole tails in the FP32 field): Manko-Novikov
     terminating rays against the oracle -- the same classification, and end angles of

@@ -253,6 +253,22 @@ def test_photon_ring_gate_matches_numpy(g, tracer, oracle):
         s.close()
 
 
+def _check_network_cells(got, rx, ry, stride):
+    """Every network pixel (nsteps 0) of a probed image lies in a probe cell whose four
+    corners the integrator classified as the pixel is: all ESCAPED for an escaped pixel,
+    all of the pixel's own status (HORIZON or MAXSTEPS) otherwise."""
+    nx, ny = (rx - 2) // stride + 2, (ry - 2) // stride + 2
+    col = lambda k, n, res: k * stride if k < n - 1 else res - 1
+    st, ns = got["status"], got["nsteps"]
+    for pix in np.flatnonzero(ns == 0):
+        j, i = divmod(int(pix), rx)
+        kx, ky = min(i // stride, nx - 2), min(j // stride, ny - 2)
+        corners = [col(ky + dy, ny, ry) * rx + col(kx + dx, nx, rx)
+                   for dy in (0, 1) for dx in (0, 1)]
+        assert all(ns[c] > 0 for c in corners), pix
+        assert all(st[c] == st[pix] for c in corners), (pix, st[pix], [st[c] for c in corners])
+
+
 def test_probed_surrogate_meets_target_and_beats_the_integrator(g, tracer):
     """The benchmark spec's target on a 512^2 Kerr image (a = 0.9M, inclination 80 deg, r0 =
     30M) after training on 2^21 integrator-labelled rays: the pixels the network decides
@@ -305,6 +321,7 @@ def test_probed_surrogate_meets_target_and_beats_the_integrator(g, tracer):
         assert integ.sum() == nfb + npr
         for k in ("status", "th", "ph", "nsteps"):
             assert np.array_equal(got[k][integ], mix[k][integ]), k
+        _check_network_cells(got, cam.res_x, cam.res_y, 8)
         assert t_sg < t_int, (t_sg, t_int)
     finally:
         s.close()
@@ -341,5 +358,7 @@ def test_probe_grid_on_ragged_and_degenerate_images(g, tracer, rx, ry, stride):
         assert integ.sum() == nfb + npr
         for k in ("status", "th", "ph", "t", "r", "nsteps"):
             assert np.array_equal(got[k][integ], mix[k][integ]), k
+        if npr:
+            _check_network_cells(got, rx, ry, stride)
     finally:
         s.close()

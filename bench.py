@@ -553,7 +553,8 @@ def leg_zone(tr, geotrace, args, torch):
     each whole image, the zone statistics, and the agreement of the two images (status of
     every pixel; end angle of the pixels both call escaped), with both against the FP64
     integrator on 256 seeded pixels that are not trapped (the trapped rays' end states at
-    the cap are chaotic)."""
+    the cap are chaotic); and the Kerr a = 0.9M image at the cap without a zone (the
+    default) and with a double-float zone at r < 4M."""
     import numpy as np
     cam = W.MN_1000
     tr.set_spacetime(cam.M, cam.S, cam.Q)
@@ -584,6 +585,26 @@ def leg_zone(tr, geotrace, args, torch):
     for name in ("double_float", "fp64"):
         acc = accuracy({k: v[pix] for k, v in outs[name].items()}, ref)
         res[name]["vs_fp64_integrator_256_untrapped_pixels"] = acc
+    # Kerr a = 0.9M, 80 deg, 1000x1000 at the cap: no zone (the default) against a
+    # double-float zone over the horizon approach and the photon region (r < 4M)
+    kerr = W.Camera(M=0.5, S=0.9 * 0.25, Q=0.0, r0=15.0, theta0=80 * W.DEG, fov_deg=75.0,
+                    res_x=1000, res_y=1000)
+    tr.set_spacetime(kerr.M, kerr.S, kerr.Q)
+    tr.set_camera(kerr.r0, kerr.theta0, kerr.fov_deg, kerr.res_x, kerr.res_y)
+    kres, kouts = {}, {}
+    for name, r_sw in (("no_zone", 0.0), ("double_float_zone_4M", 4 * kerr.M)):
+        tr.set_options(r_switch=r_sw)
+        out, t = _timed(torch, tr.stream,
+                        lambda: tr.trace(500000, 1.5e-4, geotrace.MODE_FP32_MIXED))
+        zone, f64 = tr.zone_stats()
+        steps = _steps(out)
+        kouts[name] = host_sample(out, slice(None))
+        kres[name] = {"seconds": t, "steps_per_s": steps / t, "zone_step_fraction": zone / steps,
+                      "zone_f64_eval_fraction": f64 / (4 * zone) if zone else 0.0}
+    tr.set_options()
+    kres["zone_vs_no_zone"] = accuracy(kouts["double_float_zone_4M"], kouts["no_zone"])
+    kres["cost"] = kres["double_float_zone_4M"]["seconds"] / kres["no_zone"]["seconds"]
+    res["kerr1000_T"] = kres
     return res
 
 
@@ -678,6 +699,20 @@ def mode_terminating(tr, geotrace, torch) -> dict:
                              "sample": f"{n_judge} seeded pixels of the GPU sample",
                              "seconds": t_cpu},
             "paper_seconds_per_mpx": 300 if name.startswith("kerr") else [1200, 3000]}
+        if name.startswith("kerr"):
+            # the same image with a double-float zone over the horizon approach and the
+            # photon region (r < 4M; Kerr runs without one by default)
+            tr.set_options(r_switch=4 * cam.M)
+            out_z, t_z = _timed(torch, tr.stream, run)
+            zone_z, _ = tr.zone_stats()
+            tr.set_options()
+            steps_z = _steps(out_z)
+            host_z = host_sample(out_z, slice(None))
+            host_0 = host_sample(out, slice(None))
+            res[name]["with_double_float_zone_4M"] = {
+                "seconds": t_z, "cost": t_z / t, "zone_step_fraction": zone_z / steps_z,
+                "vs_no_zone_whole_image": accuracy(host_z, host_0),
+                "accuracy_vs_oracle": accuracy(host_sample(out_z, judge), ref)}
     return res
 
 

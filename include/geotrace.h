@@ -61,8 +61,9 @@ extern "C" {
 /* arithmetic modes */
 #define GT_MODE_FP64 0       /* FP64 end to end */
 #define GT_MODE_FP32_MIXED 1 /* FP32 RK4 with compensated state; a zone r < r_switch stepped with
-                              * an FP64 state (its Manko-Novikov field in double-float where the
-                              * evaluation's range allows, else FP64) and H = 0 re-projection.
+                              * an FP64 state (its field and stage arithmetic in double-float
+                              * where the evaluation's range allows, else FP64) and H = 0
+                              * re-projection.
                               * Runs in rounds (FP32 launch, zone launch, ...) and returns
                               * once the work has completed. */
 
@@ -75,9 +76,8 @@ extern "C" {
                                   * launch; FP32-mixed runs its rounds under a conditional WHILE
                                   * node whose condition the device sets, so the call stays
                                   * asynchronous.  Not with GT_FLAG_ONE_SHOT. */
-#define GT_FLAG_ZONE_FP64 256    /* FP32-mixed, Manko-Novikov: evaluate the zone's field in FP64
-                                  * throughout instead of double-float (two floats, ~48 bits,
-                                  * on the FP32 pipes) */
+#define GT_FLAG_ZONE_FP64 256    /* FP32-mixed: step the zone in FP64 throughout instead of
+                                  * double-float (two floats, ~48 bits, on the FP32 pipes) */
 #define GT_FLAG_PRECISE_MN 16    /* FP32-mixed, Manko-Novikov: evaluate the metric's multipole
                                   * sums as closed-form series tails, free of the cancellation
                                   * that costs the plain FP32 form ~2 beta ulp(1) in its
@@ -376,8 +376,7 @@ int gt_sync(gt_ctx *ctx);
  * FP64 traces and for mixed traces that never entered it; compare with the sum of nsteps
  * for the zone's share of the work) and, in zone_f64_evals (may be NULL), the field
  * evaluations of those steps done in FP64 (all of them with GT_FLAG_ZONE_FP64; otherwise
- * the Manko-Novikov evaluations outside the double-float range).  Synchronises the
- * context's stream. */
+ * those outside the double-float range).  Synchronises the context's stream. */
 int gt_get_stats(gt_ctx *ctx, int64_t *zone_steps, int64_t *zone_f64_evals);
 
 /* Number of streaming multiprocessors of the context's device (for grid sizing). */

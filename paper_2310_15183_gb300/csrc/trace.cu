@@ -250,18 +250,26 @@ __device__ __forceinline__ double step64(const TraceArgs &A, const SpacetimeC &s
 
 // ------------------------------------------------------------------ the zone in double-float
 // The FP32-mixed path's zone steps an FP64 state.  Within a step the stage arithmetic --
-// the stage points, the sin/cos rotation, the Manko-Novikov field, the stage sums and
-// the step length -- runs in double-float (zone_df.cuh) on the FP32 pipes; the state is
-// converted once into double-float at the start of the step, the increments once back,
-// and added in FP64.  A field evaluation outside the double-float range (and Kerr, which
-// has no zone by default) takes FP64; n_f64 counts those evaluations.
+// the stage points, the sin/cos rotation, the field (Manko-Novikov, or Kerr when a zone
+// is set for it), the stage sums and the step length -- runs in double-float
+// (zone_df.cuh) on the FP32 pipes; the state is converted once into double-float at the
+// start of the step, the increments once back, and added in FP64.  A field evaluation
+// outside the double-float range (Manko-Novikov exponents out of bounds, or a rate that
+// is not finite) takes FP64; n_f64 counts those evaluations.
 template <int KIND>
 __device__ __forceinline__ void zone_rates(const SpacetimeC &st, const SpacetimeT<DF> *sd, DF r,
                                            DF s, DF cs, DF pr, DF pth, DF pt, DF pph,
                                            Rates<DF> &o, uint32_t &n_f64)
 {
     const bool mn = KIND == KIND_MN || (KIND == KIND_ANY && st.kind == KIND_MN);
-    if (mn && mn_rates_df(*sd, r, s, cs, pr, pth, pt, pph, o)) return;
+    if (mn) {
+        if (mn_rates_df(*sd, r, s, cs, pr, pth, pt, pph, o)) return;
+    } else if (KIND != KIND_FD) {
+        kerr_rates_sc<DF>(*sd, r, s, cs, pr, pth, pt, pph, o);
+        if (isfinite(o.dt.hi) && isfinite(o.dr.hi) && isfinite(o.dth.hi) &&
+            isfinite(o.dph.hi) && isfinite(o.dpr.hi) && isfinite(o.dpth.hi))
+            return;
+    }
     ++n_f64;
     Rates<double> o64;
     rates_any<KIND>(st, df_to(r), df_to(s), df_to(cs), df_to(pr), df_to(pth), df_to(pt),

@@ -1,12 +1,13 @@
-// df_arith.cpp -- host check of the double-float arithmetic of the Manko-Novikov zone
-// (csrc/df.cuh) against extended precision: sum, difference (cancellation included),
-// product, reciprocal, inverse square root, exp and the stage rotation of sin/cos on
-// seeded random operands, and the reverse-sweep Manko-Novikov rates evaluated in
-// double-float and in double against the same rates in long double, at seeded random
-// phase-space points of the zone
-// (r_+ < r < 5M, all inclinations) of several spacetimes.  The zone's range check --
-// every exponent of the evaluation within its bound -- decides which points the
-// double-float evaluation takes; the rest go to FP64 in the kernels.
+// df_arith.cpp -- host check of the double-float arithmetic of the FP32-mixed zone
+// (csrc/df.cuh, csrc/zone_df.cuh) against extended precision: sum, difference
+// (cancellation included), product, reciprocal, inverse square root, exp and the stage
+// rotation of sin/cos on seeded random operands; the reverse-sweep Manko-Novikov rates
+// evaluated in double-float and in double against the same rates in long double, at
+// seeded random phase-space points of the zone (r_+ < r < 5M, all inclinations) of
+// several spacetimes -- the zone's range check (every exponent of the evaluation within
+// its bound) decides which points the double-float evaluation takes, the rest go to
+// FP64 in the kernels; and the Kerr rates likewise for four spins, half the points
+// within 10 % of r_+.
 // Prints one JSON line of worst relative errors (units of the operation's result, or of
 // the largest rate component).
 #include <math.h>
@@ -196,6 +197,48 @@ int main()
             e_f64.push_back(e6);
         }
     }
+    // ---- Kerr rates from just outside r_+ to 5M (the zone an explicit r_switch sets)
+    std::vector<double> k_df, k_f64;
+    for (const double a : {0.3, 0.6, 0.9, 0.99}) {
+        const double M = 1.0;
+        gt::SpacetimeC c = {};
+        c.kind = gt::KIND_KERR;
+        c.M = M;
+        c.a = a * M;
+        c.a2 = c.a * c.a;
+        c.r_plus = M + sqrt(M * M - c.a2);
+        gt::SpacetimeT<LD> cl = {};
+        cl.kind = gt::KIND_KERR;
+        cl.M = c.M;
+        cl.a = c.a;
+        cl.a2 = c.a2;
+        const gt::SpacetimeT<DF> cd = gt::to_df(c);
+        for (int i = 0; i < 20000; ++i) {
+            const double r = c.r_plus * (1.0 + uni(1e-4, 0.1)) + (i % 2 ? uni(0.0, 5.0 * M) : 0.0);
+            const double th = uni(1e-3, M_PI - 1e-3);
+            const double pr = uni(-2, 2), pth = uni(-3, 3), pt = -1.0, pph = uni(-4, 4);
+            const double s = sin(th), cs = cos(th);
+            gt::Rates<LD> oL;
+            gt::kerr_rates_sc<LD>(cl, (LD)r, (LD)s, (LD)cs, (LD)pr, (LD)pth, (LD)pt, (LD)pph, oL);
+            const LD vL[6] = {oL.dt, oL.dr, oL.dth, oL.dph, oL.dpr, oL.dpth};
+            LD scale = 0;
+            for (int j = 0; j < 6; ++j) scale = fmaxl(scale, fabsl(vL[j]));
+            if (!(scale > 0) || !isfinite(scale)) continue;
+            gt::Rates<double> o64;
+            gt::kerr_rates_sc<double>(c, r, s, cs, pr, pth, pt, pph, o64);
+            gt::Rates<DF> od;
+            gt::kerr_rates_sc<DF>(cd, DF(r), DF(s), DF(cs), DF(pr), DF(pth), DF(pt), DF(pph), od);
+            const double v64[6] = {o64.dt, o64.dr, o64.dth, o64.dph, o64.dpr, o64.dpth};
+            const DF vd[6] = {od.dt, od.dr, od.dth, od.dph, od.dpr, od.dpth};
+            double ed = 0, e6 = 0;
+            for (int j = 0; j < 6; ++j) {
+                ed = fmax(ed, (double)(fabsl(ld(vd[j]) - vL[j]) / scale));
+                e6 = fmax(e6, (double)(fabsl(v64[j] - vL[j]) / scale));
+            }
+            k_df.push_back(ed);
+            k_f64.push_back(e6);
+        }
+    }
     auto pct = [](std::vector<double> v, double q) {
         std::sort(v.begin(), v.end());
         return v.empty() ? NAN : v[(size_t)(q * (double)(v.size() - 1))];
@@ -204,9 +247,12 @@ int main()
            "\"exp\": %.3e, \"rotate_abs\": %.3e, \"rotate_refused\": %ld, \"zone_points\": %ld, \"zone_points_df\": %ld, "
            "\"shell_points\": %ld, \"shell_points_df\": %ld, \"rates_df_median\": %.3e, "
            "\"rates_df_p99\": %.3e, \"rates_df_max\": %.3e, \"rates_f64_median\": %.3e, "
-           "\"rates_f64_p99\": %.3e, \"rates_f64_max\": %.3e}\n",
+           "\"rates_f64_p99\": %.3e, \"rates_f64_max\": %.3e, \"kerr_points\": %zu, "
+           "\"kerr_df_median\": %.3e, \"kerr_df_p99\": %.3e, \"kerr_df_max\": %.3e, "
+           "\"kerr_f64_median\": %.3e, \"kerr_f64_p99\": %.3e, \"kerr_f64_max\": %.3e}\n",
            w_add, w_cancel, w_mul, w_rcp, w_rsqrt, w_exp, w_rot, n_rot_refused, n_pts, n_df, n_shell, n_shell_df,
            pct(e_df, 0.5), pct(e_df, 0.99), pct(e_df, 1.0), pct(e_f64, 0.5), pct(e_f64, 0.99),
-           pct(e_f64, 1.0));
+           pct(e_f64, 1.0), k_df.size(), pct(k_df, 0.5), pct(k_df, 0.99), pct(k_df, 1.0),
+           pct(k_f64, 0.5), pct(k_f64, 0.99), pct(k_f64, 1.0));
     return 0;
 }

@@ -87,7 +87,8 @@ def test_double_float_zone_arithmetic_and_rates(tmp_path):
     spacetimes, where its range check accepts them, against long double: within ~64x the
     error of the same evaluation in double at the median and the 99th percentile (the
     ratio of the two precisions, 2^5), below 1e-6 of the largest rate everywhere, with the
-    range check accepting most of the zone and of the listing's trapped-ray shell."""
+    range check accepting most of the zone and of the listing's trapped-ray shell; and the
+    Kerr rates in double-float over r_+ < r < 5M likewise."""
     exe = str(tmp_path / "df_arith")
     cuda_inc = os.path.join(os.path.dirname(os.path.dirname(build.nvcc())), "include")
     subprocess.run(["g++", "-std=c++17", "-O1", "-ffp-contract=off", "-I" + cuda_inc,
@@ -104,3 +105,9 @@ def test_double_float_zone_arithmetic_and_rates(tmp_path):
     assert res["rates_df_median"] <= 64 * res["rates_f64_median"], res
     assert res["rates_df_p99"] <= 64 * res["rates_f64_p99"], res
     assert res["rates_df_max"] < 1e-6, res
+    # Kerr (a zone set with r_switch): double-float keeps ~1e-14 of the largest rate at the
+    # median; within 10 % of r_+ the cancellation in Delta = r (r - 2M) + a^2, which FP64
+    # takes through one exactly rounded FMA, costs it up to ~1e-10
+    assert res["kerr_points"] >= 70000, res
+    assert res["kerr_df_median"] <= 64 * res["kerr_f64_median"], res
+    assert res["kerr_df_p99"] < 1e-11 and res["kerr_df_max"] < 1e-9, res

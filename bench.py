@@ -1032,7 +1032,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_job / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64 zone" if mode else "f64", "data": "synthetic",
+            "dtype": "f32+f64/df zone" if mode else "f64", "data": "synthetic",
             "config": {"workload": wl.name, "M": cam.M, "S": cam.S, "Q": cam.Q, "r0": cam.r0,
                        "theta0_deg": round(cam.theta0 / W.DEG, 6), "fov_deg": cam.fov_deg,
                        "res": [cam.res_x, cam.res_y], "n_steps": wl.n_steps,

@@ -290,6 +290,32 @@ def test_mixed_zone_double_float_and_fp64(g, tracer, oracle):
     assert not np.array_equal(outs["df"]["th"], outs["f64"]["th"], equal_nan=True)
 
 
+def test_zone_double_float_tracks_the_fp64_zone(g, tracer):
+    """A camera inside the Manko-Novikov zone (listing's spacetime, r0 = 3.8M < 4M, 64x64,
+    2,000 steps, FP32-mixed): every ray takes its first step in the FP32 kernel and all
+    later ones in the zone kernel, so the zone statistics count rays x 1,999 steps, all
+    of them in double-float by default and all in FP64 with GT_FLAG_ZONE_FP64.  From the
+    same first step, the double-float zone's end states stay within 1e-12 (relative) of
+    the FP64 zone's: the double-float field and stage arithmetic carry ~2^-48 per
+    operation (measured: max 5.6e-14 over the 4,096 rays)."""
+    cam = W.Camera(M=0.5, S=0.24, Q=2.0, r0=1.9, theta0=80 * W.DEG, fov_deg=75.0,
+                   res_x=64, res_y=64)
+    n = 2000
+    outs, stats = {}, {}
+    for name, flags in (("df", 0), ("f64", g.FLAG_ZONE_FP64)):
+        outs[name] = run_gpu(tracer, cam, n, 1.5e-4, mode=1, flags=flags)
+        stats[name] = tracer.zone_stats()
+    assert stats["df"] == (cam.n_rays * (n - 1), 0), stats
+    assert stats["f64"] == (cam.n_rays * (n - 1), 4 * cam.n_rays * (n - 1)), stats
+    assert np.array_equal(outs["df"]["status"], outs["f64"]["status"])
+    assert np.array_equal(outs["df"]["nsteps"], outs["f64"]["nsteps"])
+    for k in ("t", "r", "th", "ph"):
+        a, b = outs["df"][k], outs["f64"][k]
+        rel = np.abs(a - b) / np.maximum(1.0, np.abs(b))
+        assert np.all(np.isfinite(a)) and rel.max() <= 1e-12, (k, float(rel.max()))
+    assert not np.array_equal(outs["df"]["r"], outs["f64"]["r"])  # the double-float zone ran
+
+
 def test_mixed_precise_mn_multipole_tails(g, tracer, oracle):
     """GT_FLAG_PRECISE_MN (closed-form multipole tails in the FP32 field): Manko-Novikov
     terminating rays against the oracle -- the same classification, and end angles of
